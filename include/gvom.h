@@ -1,0 +1,182 @@
+/*
+ * gvom.h -- C ABI of the GB300 voxel map update (G-VOM, Overbye & Saripalli,
+ * arXiv 2109.13176).
+ *
+ * One map is a fixed-size, robot-centred voxel window (Sec. III-A) held
+ * resident in device memory. Each lidar scan is folded into it (Sec. III-C
+ * pointcloud processing, combined per Sec. III-D), and the 2D products of
+ * Sec. III-D (height, positive obstacles, slope, roughness, negative
+ * obstacles) are extracted from it on demand.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are device pointers; everything else is host.
+ *  - Work is enqueued on the given CUDA stream (NULL = the legacy default
+ *    stream) and returns before it runs. Device inputs must stay valid and
+ *    unchanged until the stream reaches the call. Calls on one map must be
+ *    ordered (one stream, or events between streams).
+ *  - Every function returns a gvom_status (0 on success). Arguments are
+ *    checked before anything is enqueued, so a call that fails with
+ *    GVOM_ERR_INVALID_ARG leaves the map unchanged. GVOM_ERR_CUDA reports a
+ *    CUDA error seen while enqueueing; the map's state is then undefined.
+ *  - Invalid points are not errors: non-finite points, points at range 0 or
+ *    beyond max_range, and points too far from the window to quantise are
+ *    dropped and counted in gvom_stats.
+ *  - The library owns the map's device state (allocated by gvom_create,
+ *    freed by gvom_destroy). The caller owns point, pose and output buffers.
+ *
+ * Layouts:
+ *  - Voxel (ix, iy, iz), 0 <= ix < nx ..., is window-relative: it is the
+ *    world voxel origin + (ix, iy, iz). Logical linear index
+ *    ((ix * ny) + iy) * nz + iz. 2D products are [ix * ny + iy].
+ *  - Points are float32 xyz in the sensor frame, `stride` floats apart (3
+ *    for packed xyz, 4 for xyz + padding/intensity).
+ *  - T_ws is the row-major 3x4 world-from-sensor transform [R | t], FP64.
+ */
+#ifndef GVOM_H
+#define GVOM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GVOM_API __attribute__((visibility("default")))
+#else
+#define GVOM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t / CUstream. */
+typedef struct CUstream_st* gvom_stream_t;
+
+typedef enum gvom_status {
+    GVOM_OK = 0,
+    GVOM_ERR_INVALID_ARG = -1,   /* a null pointer, size or parameter out of range */
+    GVOM_ERR_OUT_OF_MEMORY = -2, /* device allocation failed */
+    GVOM_ERR_CUDA = -3,          /* a CUDA call failed */
+    GVOM_ERR_TIMEOUT = -4,       /* a bounded device wait gave up */
+    GVOM_ERR_BOUNDS = -5         /* a checked build caught an index out of range */
+} gvom_status;
+
+/* Map parameters (Sec. III-A map size and resolution; Sec. III-D obstacle,
+ * slope and negative obstacle parameters, which the paper leaves unnamed).
+ * Limits: 1 <= nx, ny, nz <= 4096 with nx * ny * nz < 2^31; res > 0;
+ * 0 < max_range with max_range / res < 2^20; 0 <= obs_min_h <= obs_max_h;
+ * 0 < hard_den <= 65535, hard_num <= hard_den; slope_n odd in [3, 15];
+ * 3 <= slope_min_px <= slope_n^2; 1 <= neg_max_px <= 64. */
+typedef struct gvom_config {
+    int32_t nx, ny, nz;   /* window size in voxels */
+    int32_t reserved0;    /* must be 0 */
+    double res;           /* voxel edge, metres */
+    double max_range;     /* returns beyond this range are dropped, metres */
+    float obs_min_h;      /* positive obstacle band above ground, metres */
+    float obs_max_h;
+    uint32_t hard_num;    /* hard obstacle iff density >= hard_num / hard_den */
+    uint32_t hard_den;
+    int32_t slope_n;      /* N of the N x N plane fit */
+    int32_t slope_min_px; /* defined pixels needed for a fit */
+    int32_t neg_max_px;   /* negative obstacle search distance, pixels */
+    float neg_thresh;     /* negative obstacle threshold on Delta H, metres */
+} gvom_config;
+
+/* Caller-owned device buffers for the 2D products, nx * ny elements each,
+ * [ix * ny + iy]. Any pointer may be NULL to skip that product (height is
+ * still computed internally when another product needs it).
+ *  height:    lowest return of the lowest occupied voxel of the column,
+ *             metres (world z); NaN where the column has no return.
+ *  density:   H / (H + M) over the column's obstacle voxels, 0 where there
+ *             is no positive obstacle.
+ *  flags:     bit0 positive obstacle, bit1 hard, bit2 soft, bit3 negative.
+ *  slope:     radians; NaN where no plane could be fitted.
+ *  roughness: mean squared plane-fit residual, m^2; NaN likewise. */
+typedef struct gvom_maps_out {
+    float* height_dev;
+    float* density_dev;
+    uint8_t* flags_dev;
+    float* slope_dev;
+    float* roughness_dev;
+} gvom_maps_out;
+
+/* Counters since gvom_create (or gvom_reset_stats). */
+typedef struct gvom_stats {
+    int64_t scans;          /* ingest calls */
+    int64_t points_in;      /* points offered */
+    int64_t rays_valid;     /* points kept (finite, in range, quantisable) */
+    int64_t hits_in_window; /* kept points whose endpoint voxel is in the window */
+    int64_t pass_visits;    /* pass-count increments (ray/voxel crossings) */
+} gvom_stats;
+
+/* Fills *out with defaults: 128 x 128 x 32 voxels at 0.2 m, max range 100 m,
+ * obstacle band [0.3, 2.0] m, hard density 1/2, 5 x 5 fit needing 3 pixels,
+ * negative search 10 pixels, threshold 0.3 m. */
+GVOM_API int gvom_config_default(gvom_config* out);
+
+/* Allocates a map and its device state (12 bytes per voxel plus counters)
+ * on the current CUDA device. The map starts empty at origin (0, 0, 0).
+ * Synchronises the device once. *out is set to NULL on failure. */
+GVOM_API int gvom_create(const gvom_config* cfg, struct gvom_map** out);
+
+/* Frees the map's device state. Synchronises the device. NULL is a no-op. */
+GVOM_API void gvom_destroy(struct gvom_map* map);
+
+/* The configuration the map was created with. */
+GVOM_API int gvom_get_config(const struct gvom_map* map, gvom_config* out);
+
+/* Window origin for a vehicle position (Sec. III-A: the origin is a whole
+ * number of voxels; Sec. III-D: the combined map is placed at the newest
+ * map): out = floor(vehicle_xyz / res) - (nx/2, ny/2, nz/2), FP64. Host-only. */
+GVOM_API int gvom_origin_for_pose(const struct gvom_map* map, const double vehicle_xyz[3], int64_t out_origin[3]);
+
+/* Current window origin (world voxel of window voxel (0,0,0)). Host-only. */
+GVOM_API int gvom_get_origin(const struct gvom_map* map, int64_t out_origin[3]);
+
+/* Empties the map and places it at `origin`. Stream-ordered. */
+GVOM_API int gvom_reset(struct gvom_map* map, const int64_t origin[3], gvom_stream_t stream);
+
+/* Moves the window to new_origin (Sec. III-D combination by index offset):
+ * voxels in both windows keep their metrics, voxels entering the window
+ * start empty, voxels leaving are dropped. Only the entering slabs are
+ * written (the state is stored with toroidal addressing). Stream-ordered. */
+GVOM_API int gvom_shift(struct gvom_map* map, const int64_t new_origin[3], gvom_stream_t stream);
+
+/* Folds one scan into the map (Sec. III-C, Sec. III-D combination rule):
+ * each point is transformed by T_ws (FP64, no fused multiply-add),
+ * filtered, and quantised to 1/256 voxel; the endpoint voxel gains a hit
+ * and its lowest-return height is lowered to the point's z (float32);
+ * every other window voxel the sensor-to-point segment meets (half-open
+ * voxels, exact integer traversal) gains a pass. pts_dev: n points,
+ * stride 3 or 4 floats, 16-byte aligned when stride is 4. n may be 0.
+ * Stream-ordered; the pose is copied at call time. */
+GVOM_API int gvom_ingest_scan(struct gvom_map* map, const float* pts_dev, int64_t n, int32_t stride,
+                     const double T_ws[12], gvom_stream_t stream);
+
+/* gvom_shift to gvom_origin_for_pose(vehicle_xyz), then gvom_ingest_scan. */
+GVOM_API int gvom_update(struct gvom_map* map, const double vehicle_xyz[3], const float* pts_dev, int64_t n,
+                int32_t stride, const double T_ws[12], gvom_stream_t stream);
+
+/* Computes the 2D products of Sec. III-D into caller buffers. The map may
+ * keep internal scratch for the height map. Stream-ordered. */
+GVOM_API int gvom_extract_maps(struct gvom_map* map, const gvom_maps_out* out, gvom_stream_t stream);
+
+/* Copies the voxel state in logical (window-relative) order into caller
+ * device buffers of nx*ny*nz elements. minz is +inf where a voxel has no
+ * return. Any pointer may be NULL. Stream-ordered. */
+GVOM_API int gvom_extract_voxels(struct gvom_map* map, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
+                        gvom_stream_t stream);
+
+/* Reads the counters. Synchronises with the map's last enqueued work
+ * (device-wide synchronisation). */
+GVOM_API int gvom_get_stats(struct gvom_map* map, gvom_stats* out);
+
+/* Zeroes the counters. Stream-ordered. */
+GVOM_API int gvom_reset_stats(struct gvom_map* map, gvom_stream_t stream);
+
+/* Human-readable name of a status code (static storage). */
+GVOM_API const char* gvom_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GVOM_H */

@@ -1,0 +1,335 @@
+"""GB300 voxel map update (G-VOM, arXiv 2109.13176) -- Python binding.
+
+A thin ctypes layer over libgvom.so (include/gvom.h). Every step of the map
+update runs in the library's CUDA kernels; this module only marshals
+arguments. PyTorch supplies device memory (tensors) and streams. There is no
+CPU fallback: if the library is not built, or no CUDA device is present,
+the calls raise.
+
+Low-level names match the C ABI (gvom_create, gvom_ingest_scan, ...);
+`VoxelMap` wraps one map for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgvom.so")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+
+GVOM_OK = 0
+GVOM_ERR_INVALID_ARG = -1
+GVOM_ERR_OUT_OF_MEMORY = -2
+GVOM_ERR_CUDA = -3
+GVOM_ERR_TIMEOUT = -4
+GVOM_ERR_BOUNDS = -5
+
+
+class GvomError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+        self.status = status
+
+
+class gvom_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("res", ctypes.c_double), ("max_range", ctypes.c_double),
+        ("obs_min_h", ctypes.c_float), ("obs_max_h", ctypes.c_float),
+        ("hard_num", ctypes.c_uint32), ("hard_den", ctypes.c_uint32),
+        ("slope_n", ctypes.c_int32), ("slope_min_px", ctypes.c_int32),
+        ("neg_max_px", ctypes.c_int32), ("neg_thresh", ctypes.c_float),
+    ]
+
+
+class gvom_maps_out(ctypes.Structure):
+    _fields_ = [("height_dev", ctypes.c_void_p), ("density_dev", ctypes.c_void_p),
+                ("flags_dev", ctypes.c_void_p), ("slope_dev", ctypes.c_void_p),
+                ("roughness_dev", ctypes.c_void_p)]
+
+
+class gvom_stats(ctypes.Structure):
+    _fields_ = [("scans", ctypes.c_int64), ("points_in", ctypes.c_int64),
+                ("rays_valid", ctypes.c_int64), ("hits_in_window", ctypes.c_int64),
+                ("pass_visits", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the entry points the headers under include/ declare."""
+    import glob
+    names = []
+    for h in sorted(glob.glob(os.path.join(INCLUDE, "*.h"))):
+        with open(h) as fh:
+            text = fh.read()
+        names += re.findall(r"^GVOM_API\s+[\w\s\*]+?\b(gvom_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+def load_library():
+    """Loads libgvom.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgvom.so is not built ({LIB_PATH}); run paper_2109_13176_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        P = ctypes.POINTER
+        d3 = P(ctypes.c_double)
+        o3 = P(ctypes.c_int64)
+        sig = {
+            "gvom_config_default": ([P(gvom_config)], ctypes.c_int),
+            "gvom_create": ([P(gvom_config), P(vp)], ctypes.c_int),
+            "gvom_destroy": ([vp], None),
+            "gvom_get_config": ([vp, P(gvom_config)], ctypes.c_int),
+            "gvom_origin_for_pose": ([vp, d3, o3], ctypes.c_int),
+            "gvom_get_origin": ([vp, o3], ctypes.c_int),
+            "gvom_reset": ([vp, o3, vp], ctypes.c_int),
+            "gvom_shift": ([vp, o3, vp], ctypes.c_int),
+            "gvom_ingest_scan": ([vp, vp, i64, i32, d3, vp], ctypes.c_int),
+            "gvom_update": ([vp, d3, vp, i64, i32, d3, vp], ctypes.c_int),
+            "gvom_extract_maps": ([vp, P(gvom_maps_out), vp], ctypes.c_int),
+            "gvom_extract_voxels": ([vp, vp, vp, vp, vp], ctypes.c_int),
+            "gvom_get_stats": ([vp, P(gvom_stats)], ctypes.c_int),
+            "gvom_reset_stats": ([vp, vp], ctypes.c_int),
+            "gvom_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
+            "gvom_kernel_launches": ([], ctypes.c_int64),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().gvom_status_string(int(status)).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def _check(status: int, what: str) -> None:
+    if status != GVOM_OK:
+        raise GvomError(status, what)
+
+
+def _d(vals, n):
+    arr = (ctypes.c_double * n)(*[float(v) for v in vals])
+    return arr
+
+
+def _i64(vals):
+    return (ctypes.c_int64 * 3)(*[int(v) for v in vals])
+
+
+def _T(T_ws):
+    import numpy as np
+    t = np.ascontiguousarray(T_ws, dtype=np.float64).reshape(12)
+    return (ctypes.c_double * 12)(*t.tolist())
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+# --- C ABI, same names --------------------------------------------------------
+def gvom_config_default() -> gvom_config:
+    c = gvom_config()
+    _check(load_library().gvom_config_default(ctypes.byref(c)), "gvom_config_default")
+    return c
+
+
+def gvom_create(cfg: gvom_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().gvom_create(ctypes.byref(cfg), ctypes.byref(h)), "gvom_create")
+    return h.value
+
+
+def gvom_destroy(handle: int) -> None:
+    load_library().gvom_destroy(handle)
+
+
+def gvom_get_config(handle: int) -> gvom_config:
+    c = gvom_config()
+    _check(load_library().gvom_get_config(handle, ctypes.byref(c)), "gvom_get_config")
+    return c
+
+
+def gvom_status_string(status: int) -> str:
+    return status_string(status)
+
+
+def gvom_origin_for_pose(handle: int, vehicle_xyz) -> tuple:
+    out = (ctypes.c_int64 * 3)()
+    _check(load_library().gvom_origin_for_pose(handle, _d(vehicle_xyz, 3), out), "gvom_origin_for_pose")
+    return tuple(out)
+
+
+def gvom_get_origin(handle: int) -> tuple:
+    out = (ctypes.c_int64 * 3)()
+    _check(load_library().gvom_get_origin(handle, out), "gvom_get_origin")
+    return tuple(out)
+
+
+def gvom_reset(handle: int, origin, stream=None) -> None:
+    _check(load_library().gvom_reset(handle, _i64(origin), _stream_handle(stream)), "gvom_reset")
+
+
+def gvom_shift(handle: int, new_origin, stream=None) -> None:
+    _check(load_library().gvom_shift(handle, _i64(new_origin), _stream_handle(stream)), "gvom_shift")
+
+
+def _points_args(points):
+    import torch
+    if not isinstance(points, torch.Tensor) or not points.is_cuda or points.dtype != torch.float32:
+        raise TypeError("points must be a CUDA float32 tensor of shape (n, 3) or (n, 4)")
+    if points.dim() != 2 or points.shape[1] not in (3, 4) or not points.is_contiguous():
+        raise ValueError("points must be contiguous with shape (n, 3) or (n, 4)")
+    return points.data_ptr() if points.numel() else None, points.shape[0], points.shape[1]
+
+
+def gvom_ingest_scan(handle: int, points, T_ws, stream=None) -> None:
+    ptr, n, stride = _points_args(points)
+    _check(load_library().gvom_ingest_scan(handle, ptr, n, stride, _T(T_ws), _stream_handle(stream)),
+           "gvom_ingest_scan")
+
+
+def gvom_update(handle: int, vehicle_xyz, points, T_ws, stream=None) -> None:
+    ptr, n, stride = _points_args(points)
+    _check(load_library().gvom_update(handle, _d(vehicle_xyz, 3), ptr, n, stride, _T(T_ws), _stream_handle(stream)),
+           "gvom_update")
+
+
+def gvom_extract_maps(handle: int, height=None, density=None, flags=None, slope=None, roughness=None,
+                      stream=None) -> None:
+    out = gvom_maps_out(*(t.data_ptr() if t is not None else None
+                          for t in (height, density, flags, slope, roughness)))
+    _check(load_library().gvom_extract_maps(handle, ctypes.byref(out), _stream_handle(stream)), "gvom_extract_maps")
+
+
+def gvom_extract_voxels(handle: int, hits=None, passes=None, minz=None, stream=None) -> None:
+    ptrs = [t.data_ptr() if t is not None else None for t in (hits, passes, minz)]
+    _check(load_library().gvom_extract_voxels(handle, *ptrs, _stream_handle(stream)), "gvom_extract_voxels")
+
+
+def gvom_get_stats(handle: int) -> dict:
+    st = gvom_stats()
+    _check(load_library().gvom_get_stats(handle, ctypes.byref(st)), "gvom_get_stats")
+    return {f: getattr(st, f) for f, _ in gvom_stats._fields_}
+
+
+def gvom_reset_stats(handle: int, stream=None) -> None:
+    _check(load_library().gvom_reset_stats(handle, _stream_handle(stream)), "gvom_reset_stats")
+
+
+def gvom_microbench_red(buf, ops: int, seed: int = 1, stream=None) -> None:
+    _check(load_library().gvom_microbench_red(buf.data_ptr(), buf.numel(), int(ops), seed & 0xffffffff,
+                                              _stream_handle(stream)), "gvom_microbench_red")
+
+
+def gvom_kernel_launches() -> int:
+    return int(load_library().gvom_kernel_launches())
+
+
+# --- convenience --------------------------------------------------------------
+def make_config(nx=128, ny=128, nz=32, res=0.2, **kw) -> gvom_config:
+    c = gvom_config_default()
+    c.nx, c.ny, c.nz, c.res = nx, ny, nz, res
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+class VoxelMap:
+    """One device-resident map. Device buffers are torch tensors."""
+
+    def __init__(self, cfg: gvom_config | None = None, **kw):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("VoxelMap needs a CUDA device")
+        self.cfg = cfg if cfg is not None else make_config(**kw)
+        self.handle = gvom_create(self.cfg)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gvom_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.cfg.nx, self.cfg.ny, self.cfg.nz)
+
+    @property
+    def origin(self):
+        return gvom_get_origin(self.handle)
+
+    def origin_for_pose(self, vehicle_xyz):
+        return gvom_origin_for_pose(self.handle, vehicle_xyz)
+
+    def reset(self, origin=(0, 0, 0), stream=None):
+        gvom_reset(self.handle, origin, stream)
+
+    def shift(self, new_origin, stream=None):
+        gvom_shift(self.handle, new_origin, stream)
+
+    def ingest(self, points, T_ws, stream=None):
+        gvom_ingest_scan(self.handle, points, T_ws, stream)
+
+    def update(self, vehicle_xyz, points, T_ws, stream=None):
+        gvom_update(self.handle, vehicle_xyz, points, T_ws, stream)
+
+    def alloc_maps(self, device=None):
+        import torch
+        dev = device or torch.device("cuda")
+        n2 = (self.cfg.nx, self.cfg.ny)
+        return {"height": torch.empty(n2, dtype=torch.float32, device=dev),
+                "density": torch.empty(n2, dtype=torch.float32, device=dev),
+                "flags": torch.empty(n2, dtype=torch.uint8, device=dev),
+                "slope": torch.empty(n2, dtype=torch.float32, device=dev),
+                "roughness": torch.empty(n2, dtype=torch.float32, device=dev)}
+
+    def extract_maps(self, out=None, stream=None):
+        out = out if out is not None else self.alloc_maps()
+        gvom_extract_maps(self.handle, out.get("height"), out.get("density"), out.get("flags"),
+                          out.get("slope"), out.get("roughness"), stream)
+        return out
+
+    def extract_voxels(self, stream=None):
+        import torch
+        shp = self.shape
+        hits = torch.empty(shp, dtype=torch.int32, device="cuda")
+        passes = torch.empty(shp, dtype=torch.int32, device="cuda")
+        minz = torch.empty(shp, dtype=torch.float32, device="cuda")
+        gvom_extract_voxels(self.handle, hits, passes, minz, stream)
+        return hits, passes, minz
+
+    def stats(self):
+        return gvom_get_stats(self.handle)
+
+    def reset_stats(self, stream=None):
+        gvom_reset_stats(self.handle, stream)

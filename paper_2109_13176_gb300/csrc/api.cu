@@ -1,0 +1,299 @@
+// C ABI of libgvom (declared in include/gvom.h): argument checks, device
+// state ownership, and stream-ordered launches of the kernels in ingest.cu
+// and extract.cu. No exception crosses the ABI; every entry point returns a
+// gvom_status.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+#include "gvom_internal.h"
+#include "../../include/gvom_microbench.h"
+
+using gvom::ExtractParams;
+using gvom::Geom;
+using gvom::IngestArgs;
+using gvom::MapState;
+
+namespace gvom {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace gvom
+
+struct gvom_map {
+    gvom_config cfg;
+    long long origin[3];
+    MapState s;
+    float* height_scratch;  // nx * ny, used when the caller asks for no height
+    long long scans;
+    long long points_in;
+    int device;
+};
+
+namespace {
+
+bool valid_config(const gvom_config* c) {
+    if (!c) return false;
+    if (c->nx < 1 || c->ny < 1 || c->nz < 1 || c->nx > 4096 || c->ny > 4096 || c->nz > 4096) return false;
+    if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return false;
+    if (c->reserved0 != 0) return false;
+    if (!(c->res > 0.0) || !isfinite(c->res)) return false;
+    if (!(c->max_range > 0.0) || !isfinite(c->max_range) || !(c->max_range / c->res < 1048576.0)) return false;
+    if (!(c->obs_min_h >= 0.0f) || !(c->obs_max_h >= c->obs_min_h) || !isfinite(c->obs_max_h)) return false;
+    if (c->hard_den == 0 || c->hard_den > 65535u || c->hard_num > c->hard_den) return false;
+    if (c->slope_n < 3 || c->slope_n > 15 || (c->slope_n % 2) == 0) return false;
+    if (c->slope_min_px < 3 || c->slope_min_px > c->slope_n * c->slope_n) return false;
+    if (c->neg_max_px < 1 || c->neg_max_px > 64) return false;
+    if (!isfinite(c->neg_thresh)) return false;
+    return true;
+}
+
+Geom geom_of(const gvom_map* m) {
+    Geom g;
+    g.nx = m->cfg.nx;
+    g.ny = m->cfg.ny;
+    g.nz = m->cfg.nz;
+    g.rx = (int)gvom::floor_mod(m->origin[0], m->cfg.nx);
+    g.ry = (int)gvom::floor_mod(m->origin[1], m->cfg.ny);
+    g.rz = (int)gvom::floor_mod(m->origin[2], m->cfg.nz);
+    return g;
+}
+
+long long voxels(const gvom_map* m) { return (long long)m->cfg.nx * m->cfg.ny * m->cfg.nz; }
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return GVOM_OK;
+    if (e == cudaErrorMemoryAllocation) return GVOM_ERR_OUT_OF_MEMORY;
+    return GVOM_ERR_CUDA;
+}
+
+// The origin must keep every voxel index far inside int64 arithmetic.
+bool valid_origin(const int64_t o[3]) {
+    for (int k = 0; k < 3; ++k)
+        if (o[k] < -(1LL << 40) || o[k] > (1LL << 40)) return false;
+    return true;
+}
+
+ExtractParams extract_params(const gvom_map* m) {
+    ExtractParams p;
+    p.g = geom_of(m);
+    p.res = (float)m->cfg.res;
+    p.obs_min_h = m->cfg.obs_min_h;
+    p.obs_max_h = m->cfg.obs_max_h;
+    p.hard_num = m->cfg.hard_num;
+    p.hard_den = m->cfg.hard_den;
+    p.slope_n = m->cfg.slope_n;
+    p.slope_min_px = m->cfg.slope_min_px;
+    p.neg_max_px = m->cfg.neg_max_px;
+    p.neg_thresh = m->cfg.neg_thresh;
+    return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gvom_config_default(gvom_config* out) {
+    if (!out) return GVOM_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->nx = 128;
+    out->ny = 128;
+    out->nz = 32;
+    out->res = 0.2;
+    out->max_range = 100.0;
+    out->obs_min_h = 0.3f;
+    out->obs_max_h = 2.0f;
+    out->hard_num = 1;
+    out->hard_den = 2;
+    out->slope_n = 5;
+    out->slope_min_px = 3;
+    out->neg_max_px = 10;
+    out->neg_thresh = 0.3f;
+    return GVOM_OK;
+}
+
+int gvom_create(const gvom_config* cfg, gvom_map** out) {
+    if (!out) return GVOM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!valid_config(cfg)) return GVOM_ERR_INVALID_ARG;
+    gvom_map* m = new (std::nothrow) gvom_map();
+    if (!m) return GVOM_ERR_OUT_OF_MEMORY;
+    m->cfg = *cfg;
+    cudaGetDevice(&m->device);
+    const long long V = voxels(m);
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&m->s.hits, sizeof(uint32_t) * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&m->s.passes, sizeof(uint32_t) * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&m->s.minz, sizeof(float) * (size_t)V);
+    if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
+    if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
+    if (e == cudaSuccess) e = cudaMemset(m->s.counters, 0, sizeof(unsigned long long) * gvom::kCounters);
+    if (e == cudaSuccess) e = gvom::launch_init_state(m->s, V, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        gvom_destroy(m);
+        cudaGetLastError();
+        return cuda_status(e);
+    }
+    *out = m;
+    return GVOM_OK;
+}
+
+void gvom_destroy(gvom_map* m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    cudaFree(m->s.hits);
+    cudaFree(m->s.passes);
+    cudaFree(m->s.minz);
+    cudaFree(m->s.counters);
+    cudaFree(m->height_scratch);
+    delete m;
+}
+
+int gvom_get_config(const gvom_map* m, gvom_config* out) {
+    if (!m || !out) return GVOM_ERR_INVALID_ARG;
+    *out = m->cfg;
+    return GVOM_OK;
+}
+
+int gvom_origin_for_pose(const gvom_map* m, const double vehicle_xyz[3], int64_t out_origin[3]) {
+    if (!m || !vehicle_xyz || !out_origin) return GVOM_ERR_INVALID_ARG;
+    const double inv_res = 1.0 / m->cfg.res;
+    const int half[3] = {m->cfg.nx / 2, m->cfg.ny / 2, m->cfg.nz / 2};
+    int64_t o[3];
+    for (int k = 0; k < 3; ++k) {
+        if (!isfinite(vehicle_xyz[k])) return GVOM_ERR_INVALID_ARG;
+        const double f = floor(vehicle_xyz[k] * inv_res);
+        if (!(fabs(f) < 1e12)) return GVOM_ERR_INVALID_ARG;
+        o[k] = (int64_t)f - half[k];
+    }
+    memcpy(out_origin, o, sizeof(o));
+    return GVOM_OK;
+}
+
+int gvom_get_origin(const gvom_map* m, int64_t out_origin[3]) {
+    if (!m || !out_origin) return GVOM_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) out_origin[k] = m->origin[k];
+    return GVOM_OK;
+}
+
+int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
+    if (!m || !origin || !valid_origin(origin)) return GVOM_ERR_INVALID_ARG;
+    for (int k = 0; k < 3; ++k) m->origin[k] = origin[k];
+    return cuda_status(gvom::launch_init_state(m->s, voxels(m), (cudaStream_t)stream));
+}
+
+int gvom_shift(gvom_map* m, const int64_t new_origin[3], gvom_stream_t stream) {
+    if (!m || !new_origin || !valid_origin(new_origin)) return GVOM_ERR_INVALID_ARG;
+    long long d[3];
+    bool whole = false, none = true;
+    const int n[3] = {m->cfg.nx, m->cfg.ny, m->cfg.nz};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = new_origin[k] - m->origin[k];
+        if (d[k] != 0) none = false;
+        if (d[k] >= n[k] || d[k] <= -n[k]) whole = true;
+    }
+    if (none) return GVOM_OK;
+    for (int k = 0; k < 3; ++k) m->origin[k] = new_origin[k];
+    if (whole) return cuda_status(gvom::launch_init_state(m->s, voxels(m), (cudaStream_t)stream));
+    return cuda_status(gvom::launch_shift(m->s, geom_of(m), d, (cudaStream_t)stream));
+}
+
+int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t stride, const double T_ws[12],
+                     gvom_stream_t stream) {
+    if (!m || !T_ws || n < 0 || (stride != 3 && stride != 4)) return GVOM_ERR_INVALID_ARG;
+    if (n > 0 && !pts_dev) return GVOM_ERR_INVALID_ARG;
+    if (n >= (1LL << 40)) return GVOM_ERR_INVALID_ARG;
+    if (stride == 4 && (((uintptr_t)pts_dev) & 15u) != 0) return GVOM_ERR_INVALID_ARG;
+    if ((((uintptr_t)pts_dev) & 3u) != 0) return GVOM_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+        if (!isfinite(T_ws[k])) return GVOM_ERR_INVALID_ARG;
+    IngestArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = pts_dev;
+    a.n = n;
+    a.stride = stride;
+    for (int k = 0; k < 12; ++k) a.T[k] = T_ws[k];
+    a.inv_res = 1.0 / m->cfg.res;
+    a.r2max = m->cfg.max_range * m->cfg.max_range;
+    for (int k = 0; k < 3; ++k) a.origin[k] = m->origin[k];
+    a.g = geom_of(m);
+    a.s = m->s;
+    m->scans += 1;
+    m->points_in += n;
+    return cuda_status(gvom::launch_ingest(a, (cudaStream_t)stream));
+}
+
+int gvom_update(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, int64_t n, int32_t stride,
+                const double T_ws[12], gvom_stream_t stream) {
+    if (!m || !vehicle_xyz || !T_ws || n < 0 || (stride != 3 && stride != 4) || (n > 0 && !pts_dev))
+        return GVOM_ERR_INVALID_ARG;
+    for (int k = 0; k < 12; ++k)
+        if (!isfinite(T_ws[k])) return GVOM_ERR_INVALID_ARG;
+    int64_t o[3];
+    int rc = gvom_origin_for_pose(m, vehicle_xyz, o);
+    if (rc != GVOM_OK) return rc;
+    rc = gvom_shift(m, o, stream);
+    if (rc != GVOM_OK) return rc;
+    return gvom_ingest_scan(m, pts_dev, n, stride, T_ws, stream);
+}
+
+int gvom_extract_maps(gvom_map* m, const gvom_maps_out* out, gvom_stream_t stream) {
+    if (!m || !out) return GVOM_ERR_INVALID_ARG;
+    const ExtractParams p = extract_params(m);
+    cudaStream_t st = (cudaStream_t)stream;
+    float* height = out->height_dev ? out->height_dev : m->height_scratch;
+    cudaError_t e = gvom::launch_columns(m->s, p, height, out->density_dev, out->flags_dev, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (out->slope_dev || out->roughness_dev || out->flags_dev)
+        e = gvom::launch_slope_negative(p, height, out->slope_dev, out->roughness_dev, out->flags_dev, st);
+    return cuda_status(e);
+}
+
+int gvom_extract_voxels(gvom_map* m, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
+                        gvom_stream_t stream) {
+    if (!m) return GVOM_ERR_INVALID_ARG;
+    if (!hits_dev && !passes_dev && !minz_dev) return GVOM_OK;
+    return cuda_status(
+        gvom::launch_gather_voxels(m->s, geom_of(m), hits_dev, passes_dev, minz_dev, (cudaStream_t)stream));
+}
+
+int gvom_get_stats(gvom_map* m, gvom_stats* out) {
+    if (!m || !out) return GVOM_ERR_INVALID_ARG;
+    unsigned long long c[gvom::kCounters];
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(c, m->s.counters, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    out->scans = m->scans;
+    out->points_in = m->points_in;
+    out->rays_valid = (int64_t)c[gvom::kRaysValid];
+    out->hits_in_window = (int64_t)c[gvom::kHitsInWindow];
+    out->pass_visits = (int64_t)c[gvom::kPassVisits];
+    return GVOM_OK;
+}
+
+int gvom_reset_stats(gvom_map* m, gvom_stream_t stream) {
+    if (!m) return GVOM_ERR_INVALID_ARG;
+    m->scans = 0;
+    m->points_in = 0;
+    return cuda_status(cudaMemsetAsync(m->s.counters, 0, sizeof(unsigned long long) * gvom::kCounters,
+                                       (cudaStream_t)stream));
+}
+
+int64_t gvom_kernel_launches(void) { return (int64_t)gvom::g_launches.load(); }
+
+const char* gvom_status_string(int status) {
+    switch (status) {
+        case GVOM_OK: return "ok";
+        case GVOM_ERR_INVALID_ARG: return "invalid argument";
+        case GVOM_ERR_OUT_OF_MEMORY: return "out of device memory";
+        case GVOM_ERR_CUDA: return "CUDA error";
+        case GVOM_ERR_TIMEOUT: return "device wait timed out";
+        case GVOM_ERR_BOUNDS: return "index out of bounds (checked build)";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// Internal declarations shared by the CUDA translation units of libgvom.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gvom.h"
+
+namespace gvom {
+
+// Window geometry as the kernels see it. Voxel state is stored with
+// toroidal addressing: the world voxel W lives at physical slot
+// (W mod n) on every axis, so a window shift only rewrites the voxels that
+// enter the window. A window-relative voxel c (0 <= c < n) is world voxel
+// origin + c, i.e. physical slot (c + r) mod n with r = origin mod n.
+struct Geom {
+    int nx, ny, nz;
+    int rx, ry, rz;
+};
+
+// Device state of one map.
+struct MapState {
+    uint32_t* hits;
+    uint32_t* passes;
+    float* minz;
+    unsigned long long* counters;  // kCounters entries
+};
+
+enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3, kCounters = 4 };
+
+// Per-scan arguments of the ingest kernel (passed by value).
+struct IngestArgs {
+    const float* pts;
+    long long n;
+    int stride;
+    int _pad;
+    double T[12];
+    double inv_res;
+    double r2max;
+    long long origin[3];
+    Geom g;
+    MapState s;
+};
+
+struct ExtractParams {
+    Geom g;
+    float res;
+    float obs_min_h, obs_max_h;
+    uint32_t hard_num, hard_den;
+    int slope_n, slope_min_px;
+    int neg_max_px;
+    float neg_thresh;
+};
+
+// Counts kernel launches (gvom_kernel_launches).
+void count_launch();
+
+// Launchers (return the CUDA error of the launch).
+cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st);
+cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st);
+cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t st);
+cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density,
+                           uint8_t* flags, cudaStream_t st);
+cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, float* slope, float* rough,
+                                  uint8_t* flags, cudaStream_t st);
+cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,
+                                 cudaStream_t st);
+
+__host__ __device__ inline long long floor_mod(long long a, long long n) {
+    long long r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+}  // namespace gvom

@@ -1,0 +1,72 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every entry point include/gvom.h declares, and
+rejects invalid arguments before touching the device."""
+import ctypes
+
+import pytest
+
+import paper_2109_13176_gb300 as gv
+from paper_2109_13176_gb300 import build as gvbuild
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gvbuild.build()
+    return gv.load_library()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = gv.header_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    # and the binding exposes the same names
+    for name in names:
+        assert callable(getattr(gv, name, None)), name
+
+
+def test_status_strings(lib):
+    assert gv.status_string(0) == "ok"
+    assert "invalid" in gv.status_string(gv.GVOM_ERR_INVALID_ARG)
+    assert gv.status_string(12345) == "unknown status"
+
+
+def test_config_default(lib):
+    c = gv.gvom_config_default()
+    assert (c.nx, c.ny, c.nz) == (128, 128, 32)
+    assert c.res == pytest.approx(0.2) and c.max_range == 100.0
+    assert (c.hard_num, c.hard_den, c.slope_n, c.slope_min_px, c.neg_max_px) == (1, 2, 5, 3, 10)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nx", 0), ("nz", 5000), ("res", 0.0), ("res", -0.1), ("max_range", 0.0), ("hard_den", 0),
+    ("hard_num", 3), ("slope_n", 4), ("slope_n", 17), ("slope_min_px", 2), ("neg_max_px", 0),
+    ("reserved0", 1), ("obs_max_h", 0.1), ("hard_den", 70000),
+])
+def test_create_rejects_invalid_config_before_device_work(lib, field, value):
+    c = gv.gvom_config_default()
+    setattr(c, field, value)
+    h = ctypes.c_void_p(1234)
+    rc = lib.gvom_create(ctypes.byref(c), ctypes.byref(h))
+    assert rc == gv.GVOM_ERR_INVALID_ARG
+    assert h.value is None
+
+
+def test_create_rejects_oversized_map(lib):
+    c = gv.gvom_config_default()
+    c.nx, c.ny, c.nz = 4096, 4096, 128
+    h = ctypes.c_void_p()
+    assert lib.gvom_create(ctypes.byref(c), ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG
+
+
+def test_null_arguments_rejected(lib):
+    T = (ctypes.c_double * 12)()
+    o = (ctypes.c_int64 * 3)()
+    assert lib.gvom_create(None, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_ingest_scan(None, None, 0, 3, T, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_shift(None, o, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_extract_maps(None, None, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_get_stats(None, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_origin_for_pose(None, None, o) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_config_default(None) == gv.GVOM_ERR_INVALID_ARG
+    lib.gvom_destroy(None)  # no-op
