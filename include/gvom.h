@@ -159,6 +159,31 @@ GVOM_API int gvom_update(struct gvom_map* map, const double vehicle_xyz[3], cons
  * keep internal scratch for the height map. Stream-ordered. */
 GVOM_API int gvom_extract_maps(struct gvom_map* map, const gvom_maps_out* out, gvom_stream_t stream);
 
+/* Allocation-free variant of gvom_extract_maps. The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * at the time they want the maps (a control loop that fixed its memory at
+ * start-up, a framework that owns every device buffer through its own pool,
+ * or code that may not enter the CUDA allocator), and that therefore cannot
+ * hold a gvom_map, whose creation allocates.
+ * The caller passes its own voxel grid in logical (window) order -- the
+ * layout gvom_extract_voxels writes -- with cfg describing it, and its own
+ * output buffers (as for gvom_extract_maps; any may be NULL). Nothing is
+ * allocated, freed or copied through the allocator. When out->height_dev is
+ * NULL the height map between the two extraction passes is kept in a fixed
+ * device array inside the library, 512 x 512 pixels (1 MiB) at most, which
+ * every GPU that loads the library holds until the process exits.
+ * Limits and errors: cfg must be valid and nx * ny <= 262144, else
+ * GVOM_ERR_INVALID_ARG with nothing enqueued.
+ * Set-up: the first call on each device looks the array up (with that
+ * device current); make that first call before any stream capture.
+ * Sharing: all calls on a device share the array and it keeps the last
+ * call's contents (every pixel is rewritten before it is read, so nothing
+ * needs clearing); calls that may overlap on the GPU (different streams
+ * without ordering between them) and leave height_dev NULL race on it.
+ * Stream-ordered. */
+GVOM_API int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t* hits_dev, const uint32_t* passes_dev,
+                                       const float* minz_dev, const gvom_maps_out* out, gvom_stream_t stream);
+
 /* Copies the voxel state in logical (window-relative) order into caller
  * device buffers of nx*ny*nz elements. minz is +inf where a voxel has no
  * return. Any pointer may be NULL. Stream-ordered. */

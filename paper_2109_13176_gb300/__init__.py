@@ -103,6 +103,7 @@ def load_library():
             "gvom_reset_stats": ([vp, vp], ctypes.c_int),
             "gvom_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
+            "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
         }
         for name, (args, res) in sig.items():
@@ -222,6 +223,18 @@ def gvom_extract_maps(handle: int, height=None, density=None, flags=None, slope=
     out = gvom_maps_out(*(t.data_ptr() if t is not None else None
                           for t in (height, density, flags, slope, roughness)))
     _check(load_library().gvom_extract_maps(handle, ctypes.byref(out), _stream_handle(stream)), "gvom_extract_maps")
+
+
+def gvom_extract_maps_noalloc(cfg: gvom_config, hits, passes, minz, height=None, density=None, flags=None,
+                              slope=None, roughness=None, stream=None) -> None:
+    """Allocation-free extraction from a caller-owned voxel grid in window
+    order (see include/gvom.h); the height intermediate uses the library's
+    fixed device array when `height` is None."""
+    out = gvom_maps_out(*(t.data_ptr() if t is not None else None
+                          for t in (height, density, flags, slope, roughness)))
+    _check(load_library().gvom_extract_maps_noalloc(ctypes.byref(cfg), hits.data_ptr(), passes.data_ptr(),
+                                                    minz.data_ptr(), ctypes.byref(out), _stream_handle(stream)),
+           "gvom_extract_maps_noalloc")
 
 
 def gvom_extract_voxels(handle: int, hits=None, passes=None, minz=None, stream=None) -> None:

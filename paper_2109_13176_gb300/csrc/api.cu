@@ -32,7 +32,7 @@ struct gvom_map {
     int device;
 };
 
-namespace {
+namespace gvom {
 
 bool valid_config(const gvom_config* c) {
     if (!c) return false;
@@ -49,6 +49,12 @@ bool valid_config(const gvom_config* c) {
     if (!isfinite(c->neg_thresh)) return false;
     return true;
 }
+
+}  // namespace gvom
+
+namespace {
+
+using gvom::valid_config;
 
 Geom geom_of(const gvom_map* m) {
     Geom g;

@@ -52,6 +52,9 @@ struct ExtractParams {
     float neg_thresh;
 };
 
+// Whether a configuration is within the documented limits (include/gvom.h).
+bool valid_config(const gvom_config* c);
+
 // Counts kernel launches (gvom_kernel_launches).
 void count_launch();
 
