@@ -98,6 +98,23 @@ typedef struct gvom_maps_out {
     float* roughness_dev;
 } gvom_maps_out;
 
+/* Largest scan gvom_ingest_scan accepts, in points. */
+#define GVOM_MAX_SCAN_POINTS ((int64_t)0x7fffffff)
+
+/* Launch shape of the ingest's traversal phase. A ray's in-window part is
+ * cut into segments of at most seg_len voxel slabs along its major axis,
+ * and a persistent grid of march_block-thread blocks (march_blocks_per_sm
+ * per SM, 0 = as many as fit) walks them. Results do not depend on these;
+ * speed does (the autotuner picks them per workload). Limits:
+ * 1 <= seg_len <= 4096; march_block in {128, 256, 512};
+ * 0 <= march_blocks_per_sm <= 32; reserved = 0. */
+typedef struct gvom_tuning {
+    int32_t seg_len;
+    int32_t march_block;
+    int32_t march_blocks_per_sm;
+    int32_t reserved;
+} gvom_tuning;
+
 /* Counters since gvom_create (or gvom_reset_stats). */
 typedef struct gvom_stats {
     int64_t scans;          /* ingest calls */
@@ -123,6 +140,21 @@ GVOM_API void gvom_destroy(struct gvom_map* map);
 /* The configuration the map was created with. */
 GVOM_API int gvom_get_config(const struct gvom_map* map, gvom_config* out);
 
+/* Default tuning: seg_len 16, march_block 256, blocks per SM as fit. */
+GVOM_API int gvom_tuning_default(gvom_tuning* out);
+
+/* Sets / reads the map's tuning (see gvom_tuning). Takes effect from the
+ * next ingest. Host-only. */
+GVOM_API int gvom_set_tuning(struct gvom_map* map, const gvom_tuning* tuning);
+GVOM_API int gvom_get_tuning(const struct gvom_map* map, gvom_tuning* out);
+
+/* Sizes the map's per-scan scratch (16 bytes per point for ray records
+ * plus 8 bytes per traversal segment, at most ceil(max(nx,ny,nz)/seg_len)
+ * segments per point) for scans of up to max_points points, so that no
+ * later ingest has to grow it. Growing waits for `stream` and reallocates.
+ * Call it before capturing ingests into a CUDA graph. */
+GVOM_API int gvom_reserve(struct gvom_map* map, int64_t max_points, gvom_stream_t stream);
+
 /* Window origin for a vehicle position (Sec. III-A: the origin is a whole
  * number of voxels; Sec. III-D: the combined map is placed at the newest
  * map): out = floor(vehicle_xyz / res) - (nx/2, ny/2, nz/2), FP64. Host-only. */
@@ -146,8 +178,10 @@ GVOM_API int gvom_shift(struct gvom_map* map, const int64_t new_origin[3], gvom_
  * and its lowest-return height is lowered to the point's z (float32);
  * every other window voxel the sensor-to-point segment meets (half-open
  * voxels, exact integer traversal) gains a pass. pts_dev: n points,
- * stride 3 or 4 floats, 16-byte aligned when stride is 4. n may be 0.
- * Stream-ordered; the pose is copied at call time. */
+ * stride 3 or 4 floats, 16-byte aligned when stride is 4; 0 <= n <=
+ * GVOM_MAX_SCAN_POINTS. Stream-ordered; the pose is copied at call time.
+ * When n exceeds the scratch sized so far (gvom_reserve), the call first
+ * waits for `stream` and grows it. */
 GVOM_API int gvom_ingest_scan(struct gvom_map* map, const float* pts_dev, int64_t n, int32_t stride,
                      const double T_ws[12], gvom_stream_t stream);
 

@@ -52,6 +52,11 @@ class gvom_maps_out(ctypes.Structure):
                 ("roughness_dev", ctypes.c_void_p)]
 
 
+class gvom_tuning(ctypes.Structure):
+    _fields_ = [("seg_len", ctypes.c_int32), ("march_block", ctypes.c_int32),
+                ("march_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class gvom_stats(ctypes.Structure):
     _fields_ = [("scans", ctypes.c_int64), ("points_in", ctypes.c_int64),
                 ("rays_valid", ctypes.c_int64), ("hits_in_window", ctypes.c_int64),
@@ -102,6 +107,10 @@ def load_library():
             "gvom_get_stats": ([vp, P(gvom_stats)], ctypes.c_int),
             "gvom_reset_stats": ([vp, vp], ctypes.c_int),
             "gvom_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "gvom_tuning_default": ([P(gvom_tuning)], ctypes.c_int),
+            "gvom_set_tuning": ([vp, P(gvom_tuning)], ctypes.c_int),
+            "gvom_get_tuning": ([vp, P(gvom_tuning)], ctypes.c_int),
+            "gvom_reserve": ([vp, i64, vp], ctypes.c_int),
             "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
             "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
@@ -175,6 +184,26 @@ def gvom_get_config(handle: int) -> gvom_config:
 
 def gvom_status_string(status: int) -> str:
     return status_string(status)
+
+
+def gvom_tuning_default() -> gvom_tuning:
+    t = gvom_tuning()
+    _check(load_library().gvom_tuning_default(ctypes.byref(t)), "gvom_tuning_default")
+    return t
+
+
+def gvom_set_tuning(handle: int, tuning: gvom_tuning) -> None:
+    _check(load_library().gvom_set_tuning(handle, ctypes.byref(tuning)), "gvom_set_tuning")
+
+
+def gvom_get_tuning(handle: int) -> gvom_tuning:
+    t = gvom_tuning()
+    _check(load_library().gvom_get_tuning(handle, ctypes.byref(t)), "gvom_get_tuning")
+    return t
+
+
+def gvom_reserve(handle: int, max_points: int, stream=None) -> None:
+    _check(load_library().gvom_reserve(handle, int(max_points), _stream_handle(stream)), "gvom_reserve")
 
 
 def gvom_origin_for_pose(handle: int, vehicle_xyz) -> tuple:
@@ -309,6 +338,12 @@ class VoxelMap:
 
     def shift(self, new_origin, stream=None):
         gvom_shift(self.handle, new_origin, stream)
+
+    def set_tuning(self, seg_len=16, march_block=256, march_blocks_per_sm=0):
+        gvom_set_tuning(self.handle, gvom_tuning(seg_len, march_block, march_blocks_per_sm, 0))
+
+    def reserve(self, max_points, stream=None):
+        gvom_reserve(self.handle, max_points, stream)
 
     def ingest(self, points, T_ws, stream=None):
         gvom_ingest_scan(self.handle, points, T_ws, stream)

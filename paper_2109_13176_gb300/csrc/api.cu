@@ -26,7 +26,9 @@ struct gvom_map {
     gvom_config cfg;
     long long origin[3];
     MapState s;
+    gvom::RayScratch w;     // per-scan ray records and segment work list
     float* height_scratch;  // nx * ny, used when the caller asks for no height
+    gvom_tuning tune;
     long long scans;
     long long points_in;
     int device;
@@ -97,9 +99,73 @@ ExtractParams extract_params(const gvom_map* m) {
     return p;
 }
 
+bool valid_tuning(const gvom_tuning* t) {
+    return t && t->seg_len >= 1 && t->seg_len <= 4096 && (t->march_block == 128 || t->march_block == 256 ||
+                                                          t->march_block == 512) &&
+           t->march_blocks_per_sm >= 0 && t->march_blocks_per_sm <= 32 && t->reserved == 0;
+}
+
+// Grows the ray records and the segment work list to hold a scan of n points
+// under the current segment length. Waits for the map's stream first when
+// buffers in use are replaced.
+int ensure_capacity(gvom_map* m, long long n, cudaStream_t st) {
+    const long long per_ray = gvom::max_segments_per_ray(geom_of(m), m->tune.seg_len);
+    if (n <= m->w.cap_points && n * per_ray <= m->w.cap_items) return GVOM_OK;
+    long long cap = m->w.cap_points > n ? m->w.cap_points : n;
+    if (cap < 4096) cap = 4096;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaFree(m->w.rays);
+    cudaFree(m->w.items);
+    m->w.rays = nullptr;
+    m->w.items = nullptr;
+    m->w.cap_points = 0;
+    m->w.cap_items = 0;
+    e = cudaMalloc(&m->w.rays, sizeof(int4) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc(&m->w.items, sizeof(uint2) * (size_t)(cap * per_ray));
+    if (e != cudaSuccess) {
+        cudaFree(m->w.rays);
+        cudaFree(m->w.items);
+        m->w.rays = nullptr;
+        m->w.items = nullptr;
+        cudaGetLastError();
+        return GVOM_ERR_OUT_OF_MEMORY;
+    }
+    m->w.cap_points = cap;
+    m->w.cap_items = cap * per_ray;
+    return GVOM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int gvom_tuning_default(gvom_tuning* out) {
+    if (!out) return GVOM_ERR_INVALID_ARG;
+    out->seg_len = 16;
+    out->march_block = 256;
+    out->march_blocks_per_sm = 0;
+    out->reserved = 0;
+    return GVOM_OK;
+}
+
+int gvom_set_tuning(gvom_map* m, const gvom_tuning* t) {
+    if (!m || !valid_tuning(t)) return GVOM_ERR_INVALID_ARG;
+    m->tune = *t;
+    return GVOM_OK;
+}
+
+int gvom_get_tuning(const gvom_map* m, gvom_tuning* out) {
+    if (!m || !out) return GVOM_ERR_INVALID_ARG;
+    *out = m->tune;
+    return GVOM_OK;
+}
+
+int gvom_reserve(gvom_map* m, int64_t max_points, gvom_stream_t stream) {
+    if (!m || max_points < 0 || max_points > GVOM_MAX_SCAN_POINTS) return GVOM_ERR_INVALID_ARG;
+    return ensure_capacity(m, max_points, (cudaStream_t)stream);
+}
+
 
 int gvom_config_default(gvom_config* out) {
     if (!out) return GVOM_ERR_INVALID_ARG;
@@ -127,6 +193,7 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     gvom_map* m = new (std::nothrow) gvom_map();
     if (!m) return GVOM_ERR_OUT_OF_MEMORY;
     m->cfg = *cfg;
+    gvom_tuning_default(&m->tune);
     cudaGetDevice(&m->device);
     const long long V = voxels(m);
     cudaError_t e = cudaSuccess;
@@ -135,6 +202,7 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->s.minz, sizeof(float) * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
+    if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->s.counters, 0, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = gvom::launch_init_state(m->s, V, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -155,6 +223,9 @@ void gvom_destroy(gvom_map* m) {
     cudaFree(m->s.minz);
     cudaFree(m->s.counters);
     cudaFree(m->height_scratch);
+    cudaFree(m->w.rays);
+    cudaFree(m->w.items);
+    cudaFree(m->w.item_count);
     delete m;
 }
 
@@ -211,11 +282,17 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
                      gvom_stream_t stream) {
     if (!m || !T_ws || n < 0 || (stride != 3 && stride != 4)) return GVOM_ERR_INVALID_ARG;
     if (n > 0 && !pts_dev) return GVOM_ERR_INVALID_ARG;
-    if (n >= (1LL << 40)) return GVOM_ERR_INVALID_ARG;
+    if (n > GVOM_MAX_SCAN_POINTS) return GVOM_ERR_INVALID_ARG;
     if (stride == 4 && (((uintptr_t)pts_dev) & 15u) != 0) return GVOM_ERR_INVALID_ARG;
     if ((((uintptr_t)pts_dev) & 3u) != 0) return GVOM_ERR_INVALID_ARG;
     for (int k = 0; k < 12; ++k)
         if (!isfinite(T_ws[k])) return GVOM_ERR_INVALID_ARG;
+    if (n == 0) {
+        m->scans += 1;
+        return GVOM_OK;
+    }
+    int rc = ensure_capacity(m, n, (cudaStream_t)stream);
+    if (rc != GVOM_OK) return rc;
     IngestArgs a;
     memset(&a, 0, sizeof(a));
     a.pts = pts_dev;
@@ -227,9 +304,14 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     for (int k = 0; k < 3; ++k) a.origin[k] = m->origin[k];
     a.g = geom_of(m);
     a.s = m->s;
+    a.w = m->w;
+    a.seg_len = m->tune.seg_len;
+    gvom::MarchShape shape;
+    shape.block = m->tune.march_block;
+    shape.blocks_per_sm = m->tune.march_blocks_per_sm;
     m->scans += 1;
     m->points_in += n;
-    return cuda_status(gvom::launch_ingest(a, (cudaStream_t)stream));
+    return cuda_status(gvom::launch_ingest(a, shape, (cudaStream_t)stream));
 }
 
 int gvom_update(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, int64_t n, int32_t stride,

@@ -28,18 +28,36 @@ struct MapState {
 
 enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3, kCounters = 4 };
 
-// Per-scan arguments of the ingest kernel (passed by value).
+// Per-scan scratch of the two-phase ingest, owned by the map: one record
+// per point (quantised endpoint and its number of traversal segments), the
+// segment work list, and its length.
+struct RayScratch {
+    int4* rays;               // cap_points entries: (qx, qy, qz, nseg)
+    uint2* items;             // cap_items entries: (point index, segment index)
+    unsigned long long* item_count; // one word
+    long long cap_points;
+    long long cap_items;
+};
+
+// Per-scan arguments of the ingest kernels (passed by value).
 struct IngestArgs {
     const float* pts;
     long long n;
     int stride;
-    int _pad;
+    int seg_len;              // major-axis voxel slabs per traversal segment
     double T[12];
     double inv_res;
     double r2max;
     long long origin[3];
     Geom g;
     MapState s;
+    RayScratch w;
+};
+
+// Launch shape of the segment walk (tunable).
+struct MarchShape {
+    int block;                // threads per block
+    int blocks_per_sm;        // 0: as many as fit
 };
 
 struct ExtractParams {
@@ -61,7 +79,9 @@ void count_launch();
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st);
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st);
-cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t st);
+cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st);
+// Segments a ray of the given window can have at most, for segment length L.
+long long max_segments_per_ray(const Geom& g, int seg_len);
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density,
                            uint8_t* flags, cudaStream_t st);
 cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, float* slope, float* rough,

@@ -1,19 +1,33 @@
 // Per-scan ingest (G-VOM Sec. III-C, combined per Sec. III-D) and window
 // shift (Sec. III-A origin, Sec. III-D index offset) for sm_103a.
 //
-// One thread per lidar point: transform in FP64 without fused operations,
-// filter, quantise to 1/256 voxel, bin the hit, then walk the exact integer
-// traversal from the sensor to the point and count a pass in every other
-// window voxel it meets. Pass counts of lanes that stand in the same voxel
-// at the same step are merged (__match_any_sync) so that the many rays
-// leaving the sensor together cost one L2 atomic per warp, not one per ray.
+// The ingest runs in two phases so that every warp does a similar amount
+// of traversal work (a ray crosses anywhere from one to several hundred
+// voxels, and one thread per ray leaves the GPU idle behind the longest):
+//
+//  k_rays   one thread per lidar point: FP64 transform without fused
+//           operations, filter, quantisation to 1/256 voxel, the hit and
+//           lowest-return update of the endpoint voxel, and the split of
+//           the ray's in-window traversal into segments of at most
+//           seg_len voxel slabs along its major axis, appended to a work
+//           list in segment-major order per warp of rays.
+//  k_march  a persistent grid walks the segments. Each segment's first
+//           voxel is computed exactly from the rational time at which the
+//           major axis enters it, then the exact integer traversal runs to
+//           the segment's end and counts one pass per window voxel. Lanes
+//           that stand in the same voxel at the same step merge their
+//           increments (__match_any_sync), so neighbouring rays near the
+//           sensor cost one L2 atomic per warp.
+//
+// Counts are order-free sums, so the result is bit-identical to walking
+// every ray whole in one thread.
 #include "gvom_internal.h"
 
 namespace gvom {
 
 namespace {
 
-constexpr int kIngestBlock = 256;
+constexpr int kRaysBlock = 256;
 constexpr double kQLim = 1073741824.0;  // 2^30: quantised coordinates stay below this magnitude
 
 __device__ __forceinline__ bool in_window(const Geom& g, int cx, int cy, int cz) {
@@ -29,6 +43,8 @@ __device__ __forceinline__ uint32_t phys_index(const Geom& g, int cx, int cy, in
     pz -= (pz >= g.nz) ? g.nz : 0;
     return ((uint32_t)px * (uint32_t)g.ny + (uint32_t)py) * (uint32_t)g.nz + (uint32_t)pz;
 }
+
+__device__ __forceinline__ int dim_of(const Geom& g, int axis) { return axis == 0 ? g.nx : (axis == 1 ? g.ny : g.nz); }
 
 // Lowest-return height as an atomic float minimum. For v >= 0 the IEEE bit
 // patterns order like signed ints; for v < 0 they order in reverse as
@@ -56,65 +72,65 @@ __device__ __forceinline__ bool quantise(double w, double inv_res, long long ori
     return true;
 }
 
-// Per-axis state of the exact traversal. The next voxel boundary on this
-// axis is reached at t = num / den along the segment (den = |d|); a walk
-// that moves up takes the new voxel at t, one that moves down just after t.
-struct Axis {
-    int c;         // current voxel
-    int rem;       // boundaries left to cross
-    int dir;       // +1, -1, or 0
-    uint32_t num;  // < 2^31 + 256
-    uint32_t den;  // |d| < 2^31
+__device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
+
+// v[k] for a run-time k without indexing a local array (keeps v in registers).
+template <typename T>
+__device__ __forceinline__ T sel3(const T v[3], int k) {
+    return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]);
+}
+
+// A ray from sensor a to endpoint b (1/256-voxel units): its major axis M
+// (largest |d|, lowest index on ties), the number K of major-axis voxel
+// steps from start to end, and the range [klo, khi] of steps k whose major
+// slab (c0 + dir k) lies in the window.
+struct RayFrame {
+    int a[3], b[3], d[3];
+    int M;
+    int K;
+    int klo, khi;
 };
 
-__device__ __forceinline__ void axis_init(Axis& ax, int a, int b) {
-    ax.c = a >> 8;
-    const int ce = b >> 8;
-    const int d = b - a;
-    if (d > 0) {
-        ax.dir = 1;
-        ax.den = (uint32_t)d;
-        ax.num = (uint32_t)(256 * (ax.c + 1) - a);
-        ax.rem = ce - ax.c;
-    } else if (d < 0) {
-        ax.dir = -1;
-        ax.den = (uint32_t)(-d);
-        ax.num = (uint32_t)(a - 256 * ax.c);
-        ax.rem = ax.c - ce;
-    } else {
-        ax.dir = 0;
-        ax.den = 1;
-        ax.num = 0;
-        ax.rem = 0;
+// False when no voxel of the ray but possibly its endpoint voxel can be in
+// the window: zero extent, an unmoving axis outside the window, or no major
+// slab inside it.
+__device__ __forceinline__ bool ray_frame(const Geom& g, const int a[3], const int b[3], RayFrame& f) {
+    int best = -1;
+    f.M = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        f.a[k] = a[k];
+        f.b[k] = b[k];
+        f.d[k] = b[k] - a[k];
+        const int ad = iabs(f.d[k]);
+        if (ad > best) {
+            best = ad;
+            f.M = k;
+        }
     }
+    if (best == 0) return false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (f.d[k] == 0 && (unsigned)(a[k] >> 8) >= (unsigned)dim_of(g, k)) return false;
+    const int M = f.M;
+    const int c0 = sel3(a, M) >> 8, ce = sel3(b, M) >> 8, n = dim_of(g, M);
+    if (sel3(f.d, M) > 0) {
+        f.K = ce - c0;
+        f.klo = max(0, -c0);
+        f.khi = min(f.K, n - 1 - c0);
+    } else {
+        f.K = c0 - ce;
+        f.klo = max(0, c0 - (n - 1));
+        f.khi = min(f.K, c0);
+    }
+    return f.khi >= f.klo;
 }
 
-// Whether axis i's next crossing comes strictly before axis j's: earlier t,
-// or the same t with i moving up and j moving down.
-__device__ __forceinline__ bool before(const Axis& i, const Axis& j) {
-    const unsigned long long l = (unsigned long long)i.num * j.den;
-    const unsigned long long r = (unsigned long long)j.num * i.den;
-    return l < r || (l == r && i.dir > j.dir);
-}
-
-__device__ __forceinline__ bool same_event(const Axis& i, const Axis& j) {
-    return i.dir == j.dir && (unsigned long long)i.num * j.den == (unsigned long long)j.num * i.den;
-}
-
-__device__ __forceinline__ void axis_step(Axis& ax) {
-    ax.c += ax.dir;
-    ax.num += 256u;
-    ax.rem -= 1;
-}
-
-// Whether the walk has left the window for good on this axis.
-__device__ __forceinline__ bool gone(const Axis& ax, int n) {
-    return (ax.dir > 0 && ax.c >= n) || (ax.dir < 0 && ax.c < 0);
-}
-
-__global__ void __launch_bounds__(kIngestBlock) k_ingest(const IngestArgs a) {
-    const long long i = (long long)blockIdx.x * kIngestBlock + threadIdx.x;
+// Phase 1: points -> hits, lowest returns, ray records and segment list.
+__global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
+    const long long i = (long long)blockIdx.x * kRaysBlock + threadIdx.x;
     const Geom g = a.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     bool valid = false;
     int q[3] = {0, 0, 0};
@@ -152,7 +168,7 @@ __global__ void __launch_bounds__(kIngestBlock) k_ingest(const IngestArgs a) {
     }
 
     int hit_in_window = 0;
-    unsigned long long visits = 0;
+    int nseg = 0;
     if (valid) {
         const int ex = q[0] >> 8, ey = q[1] >> 8, ez = q[2] >> 8;
         if (in_window(g, ex, ey, ez)) {
@@ -161,64 +177,284 @@ __global__ void __launch_bounds__(kIngestBlock) k_ingest(const IngestArgs a) {
             atomic_min_f32(a.s.minz + k, wz);
             hit_in_window = 1;
         }
+        RayFrame f;
+        if (ray_frame(g, qo, q, f)) nseg = (f.khi - f.klo) / a.seg_len + 1;
+    }
+    if (i < a.n) a.w.rays[i] = make_int4(q[0], q[1], q[2], nseg);
 
-        Axis X, Y, Z;
-        axis_init(X, qo[0], q[0]);
-        axis_init(Y, qo[1], q[1]);
-        axis_init(Z, qo[2], q[2]);
-        int total = X.rem + Y.rem + Z.rem;
-        // Walk every voxel but the last (the endpoint voxel gets the hit).
-        while (total > 0) {
-            const bool inside = in_window(g, X.c, Y.c, Z.c);
-            const uint32_t key = inside ? phys_index(g, X.c, Y.c, Z.c) : 0xffffffffu;
-            const unsigned int active = __activemask();
-            const unsigned int peers = __match_any_sync(active, key);
-            if (inside) {
-                const int lane = threadIdx.x & 31;
-                if (lane == __ffs(peers) - 1) atomicAdd(a.s.passes + key, (uint32_t)__popc(peers));
-                visits += 1;
-            }
-            // the axis (or axes) whose boundary comes next
-            Axis M = X;
-            bool have = X.rem > 0;
-            if (Y.rem > 0 && (!have || before(Y, M))) {
-                M = Y;
-                have = true;
-            }
-            if (Z.rem > 0 && (!have || before(Z, M))) M = Z;
-            const bool sx = X.rem > 0 && same_event(X, M);
-            const bool sy = Y.rem > 0 && same_event(Y, M);
-            const bool sz = Z.rem > 0 && same_event(Z, M);
-            if (sx) axis_step(X);
-            if (sy) axis_step(Y);
-            if (sz) axis_step(Z);
-            total -= (int)sx + (int)sy + (int)sz;
-            // once past the window on any axis the walk never comes back
-            if (gone(X, g.nx) || gone(Y, g.ny) || gone(Z, g.nz)) break;
+    // Reserve this block's slots in the work list with one atomic, then lay
+    // each warp's segments out segment-major (all first segments of the
+    // warp's rays, then all second segments, ...), so that the lanes that
+    // later walk neighbouring items walk neighbouring rays at similar range.
+    __shared__ unsigned int warp_tot[kRaysBlock / 32];
+    __shared__ unsigned long long block_base;
+    unsigned int tot = (unsigned int)nseg;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+    if (lane == 0) warp_tot[warp] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int s = 0;
+        for (int w = 0; w < kRaysBlock / 32; ++w) s += warp_tot[w];
+        block_base = s ? atomicAdd(a.w.item_count, (unsigned long long)s) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long off = block_base;
+    for (int w = 0; w < warp; ++w) off += warp_tot[w];
+    const unsigned int lt = (1u << lane) - 1u;
+    for (int j = 0; j < wmax; ++j) {
+        const unsigned int m = __ballot_sync(0xffffffffu, nseg > j);
+        if (nseg > j) {
+            const unsigned long long slot = off + __popc(m & lt);
+            if (slot < (unsigned long long)a.w.cap_items) a.w.items[slot] = make_uint2((unsigned int)i, (unsigned int)j);
         }
+        off += __popc(m);
     }
 
     // Counters: one atomic per block and counter.
-    __shared__ unsigned long long red[3][kIngestBlock / 32];
-    unsigned long long v0 = valid ? 1ull : 0ull, v1 = (unsigned long long)hit_in_window, v2 = visits;
+    __shared__ unsigned long long red[2][kRaysBlock / 32];
+    unsigned long long v0 = valid ? 1ull : 0ull, v1 = (unsigned long long)hit_in_window;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         v0 += __shfl_xor_sync(0xffffffffu, v0, o);
         v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-        v2 += __shfl_xor_sync(0xffffffffu, v2, o);
     }
-    const int warp = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         red[0][warp] = v0;
         red[1][warp] = v1;
-        red[2][warp] = v2;
     }
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x < 2) {
         unsigned long long s = 0;
-        for (int w = 0; w < kIngestBlock / 32; ++w) s += red[threadIdx.x][w];
+        for (int w = 0; w < kRaysBlock / 32; ++w) s += red[threadIdx.x][w];
         if (s) atomicAdd(a.s.counters + kRaysValid + threadIdx.x, s);
     }
+}
+
+// Phase 2: walk the segments.
+//
+// Roles: M is the ray's major axis, A and B the other two (in x, y, z
+// order after M). For each axis the next voxel boundary is crossed at
+// t = num / den along the segment (den = |d|, num measured from the ray's
+// start). Axis i's next crossing comes first iff num_i den_j < num_j den_i,
+// so the walk keeps the three pairwise differences D_ij = num_i den_j -
+// num_j den_i and updates them as axes step (num grows by 256). Both next
+// crossings lie within one voxel of the current point along the ray, which
+// bounds |D_ij| by 256 max(den) < 2^31, so they fit 32-bit integers.
+// An axis that does not move gets a crossing at t = 2 (num 2, den 1),
+// beyond the ray's end, so it never steps; likewise the crossings an axis
+// would make past the endpoint come after every real one. The walk
+// therefore needs only the count of crossings left to the endpoint.
+//
+// Ties (Sec. III-A half-open voxels): an upward crossing takes effect at
+// its t, a downward one just after it. Ordering crossings by (t, down after
+// up), all axes sharing the earliest key step together.
+//
+// A segment that starts at major step k > 0 begins in the first voxel whose
+// major coordinate is the new slab. At that instant t* = numStar / denM a
+// minor axis stands at P = a + t* d; its voxel is floor(P / 256), except
+// when both it and the major axis move down: then the major step (taken
+// just after t*) comes with the minor's own crossing at t*, if any, so the
+// voxel is ceil(P / 256) - 1.
+
+// q = floor(x / y) for y > 0 and |x / y| < 2^23: an FP32 estimate corrected
+// exactly with 64-bit integer remainders.
+__device__ __forceinline__ long long floor_div_small(long long x, long long y) {
+    long long q = (long long)floorf(__fdiv_rn((float)x, (float)y));
+    long long r = x - q * y;
+    while (r < 0) {
+        q -= 1;
+        r += y;
+    }
+    while (r >= y) {
+        q += 1;
+        r -= y;
+    }
+    return q;
+}
+
+struct Walk {
+    int cM, cA, cB;     // current voxel, window coordinates
+    int dirM, dirA, dirB;
+    int nA, nB;         // window extents of the minor axes
+    int sM, sA, sB;     // 256 den per axis
+    int dMA, dMB, dAB;  // pairwise crossing-time differences
+    int tMA, tAM, tMB, tBM, tAB, tBA;  // tie thresholds: i first iff D_ij < t_ij
+    int total;          // crossings left to the endpoint
+    int segM;           // major steps left in this segment
+    int rM, rA, rB;     // ring offsets
+    int nM;
+    uint32_t kM, kA, kB;  // strides of the state array per role
+};
+
+__device__ __forceinline__ int rank_of(int dir) { return dir > 0 ? 0 : 1; }
+
+// Builds the walk of segment j of the ray to endpoint b. False if the ray
+// has no voxel to count in the window.
+__device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], const int b[3], int j, Walk& w) {
+    const Geom& g = a.g;
+    RayFrame f;
+    if (!ray_frame(g, qo, b, f)) return false;
+    const int M = f.M, A = M == 0 ? 1 : 0, B = M == 2 ? 1 : 2;
+    const int kstart = f.klo + j * a.seg_len;
+    const int kend = min(f.khi, kstart + a.seg_len - 1);
+    w.segM = kend - kstart;
+
+    const int aM = sel3(f.a, M), dM = sel3(f.d, M);
+    const int dirM = dM > 0 ? 1 : -1;
+    const long long denM = dM > 0 ? dM : -dM;
+    const int c0M = aM >> 8;
+    const long long numFirst = dirM > 0 ? 256LL * (c0M + 1) - aM : (long long)aM - 256LL * c0M;
+    const long long numStar = numFirst + 256LL * (kstart - 1);
+
+    int c[3], dir[3];
+    long long num[3], den[3];
+    int total = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int k = r == 0 ? M : (r == 1 ? A : B);
+        const int ak = sel3(f.a, k), dk = sel3(f.d, k), ce = sel3(f.b, k) >> 8;
+        int ck;
+        if (r == 0) {
+            ck = c0M + dirM * kstart;
+        } else if (kstart == 0 || dk == 0) {
+            ck = ak >> 8;
+        } else {
+            // position at numStar / denM, in 1/256 voxel, times denM
+            const long long X = (long long)ak * denM + numStar * (long long)dk;
+            const long long Y = 256LL * denM;
+            ck = (int)((dirM < 0 && dk < 0) ? -floor_div_small(-X, Y) - 1 : floor_div_small(X, Y));
+        }
+        c[r] = ck;
+        if (dk != 0) {
+            dir[r] = dk > 0 ? 1 : -1;
+            den[r] = dk > 0 ? dk : -dk;
+            num[r] = dk > 0 ? 256LL * (ck + 1) - ak : (long long)ak - 256LL * ck;
+            total += dk > 0 ? ce - ck : ck - ce;
+        } else {
+            dir[r] = 1;
+            den[r] = 1;
+            num[r] = 2;
+        }
+    }
+    w.cM = c[0];
+    w.cA = c[1];
+    w.cB = c[2];
+    w.dirM = dir[0];
+    w.dirA = dir[1];
+    w.dirB = dir[2];
+    w.sM = (int)(256 * den[0]);
+    w.sA = (int)(256 * den[1]);
+    w.sB = (int)(256 * den[2]);
+    w.dMA = (int)(num[0] * den[1] - num[1] * den[0]);
+    w.dMB = (int)(num[0] * den[2] - num[2] * den[0]);
+    w.dAB = (int)(num[1] * den[2] - num[2] * den[1]);
+    // i first on equal t iff i moves up and j down: D_ij < t_ij with
+    // t_ij = 1 then, else 0; j first iff D_ij > -t_ji.
+    const int rk0 = rank_of(dir[0]), rk1 = rank_of(dir[1]), rk2 = rank_of(dir[2]);
+    w.tMA = rk0 < rk1;
+    w.tAM = rk1 < rk0;
+    w.tMB = rk0 < rk2;
+    w.tBM = rk2 < rk0;
+    w.tAB = rk1 < rk2;
+    w.tBA = rk2 < rk1;
+    w.total = total;
+    w.nM = dim_of(g, M);
+    w.nA = dim_of(g, A);
+    w.nB = dim_of(g, B);
+    const int rr[3] = {g.rx, g.ry, g.rz};
+    const uint32_t st[3] = {(uint32_t)g.ny * (uint32_t)g.nz, (uint32_t)g.nz, 1u};
+    w.rM = sel3(rr, M);
+    w.rA = sel3(rr, A);
+    w.rB = sel3(rr, B);
+    w.kM = sel3(st, M);
+    w.kA = sel3(st, A);
+    w.kB = sel3(st, B);
+    return true;
+}
+
+__device__ __forceinline__ uint32_t walk_index(const Walk& w) {
+    int pM = w.cM + w.rM;
+    pM -= pM >= w.nM ? w.nM : 0;
+    int pA = w.cA + w.rA;
+    pA -= pA >= w.nA ? w.nA : 0;
+    int pB = w.cB + w.rB;
+    pB -= pB >= w.nB ? w.nB : 0;
+    return (uint32_t)pM * w.kM + (uint32_t)pA * w.kA + (uint32_t)pB * w.kB;
+}
+
+__global__ void k_march(const IngestArgs a) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long total_items = *a.w.item_count;
+    const long long n_items =
+        (long long)(total_items < (unsigned long long)a.w.cap_items ? total_items : a.w.cap_items);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+
+    int qo[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) quantise(a.T[4 * k + 3], a.inv_res, a.origin[k], &qo[k]);
+
+    unsigned long long visits = 0;
+    for (long long base = gw * 32; base < n_items; base += nwarps * 32) {
+        const long long idx = base + lane;
+        Walk w;
+        bool live = false;
+        if (idx < n_items) {
+            const uint2 it = a.w.items[idx];
+            const int4 r = a.w.rays[it.x];
+            const int b[3] = {r.x, r.y, r.z};
+            live = walk_init(a, qo, b, (int)it.y, w);
+        }
+        // Visit the current voxel, then take the next crossing group,
+        // unless it moves the major axis past this segment. The ray's last
+        // voxel (no crossings left) is the endpoint voxel: no pass.
+        while (__any_sync(0xffffffffu, live)) {
+            uint32_t key = 0xffffffffu;
+            bool inside = false;
+            if (live) {
+                if (w.total == 0) {
+                    live = false;
+                } else {
+                    inside = (unsigned)w.cA < (unsigned)w.nA && (unsigned)w.cB < (unsigned)w.nB;
+                    if (inside) key = walk_index(w);
+                }
+            }
+            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            if (inside) {
+                if (lane == __ffs(peers) - 1) atomicAdd(a.s.passes + key, (uint32_t)__popc(peers));
+                visits += 1;
+            }
+            if (!live) continue;
+            const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
+            const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
+            const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
+            if (gM) {
+                if (w.segM == 0) {
+                    live = false;
+                    continue;
+                }
+                w.segM -= 1;
+                w.cM += w.dirM;
+            }
+            w.cA += gA ? w.dirA : 0;
+            w.cB += gB ? w.dirB : 0;
+            w.dMA += (gM ? w.sA : 0) - (gA ? w.sM : 0);
+            w.dMB += (gM ? w.sB : 0) - (gB ? w.sM : 0);
+            w.dAB += (gA ? w.sB : 0) - (gB ? w.sA : 0);
+            w.total -= (int)gM + (int)gA + (int)gB;
+            // a minor axis past the window never comes back
+            if ((w.dirA > 0 && w.cA >= w.nA) || (w.dirA < 0 && w.cA < 0) || (w.dirB > 0 && w.cB >= w.nB) ||
+                (w.dirB < 0 && w.cB < 0))
+                live = false;
+        }
+    }
+
+    // Counter: one atomic per warp of the persistent grid.
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+    if (lane == 0 && visits) atomicAdd(a.s.counters + kPassVisits, visits);
 }
 
 // Fill the state with the empty voxel: no hits, no passes, min height +inf.
@@ -268,7 +504,26 @@ __global__ void k_shift(MapState s, Geom g, int dx, int dy, int dz) {
     }
 }
 
+// Blocks of the persistent segment walk: every SM filled to its occupancy.
+int march_grid(const MarchShape& shape) {
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    int per_sm = shape.blocks_per_sm;
+    if (per_sm <= 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march, shape.block, 0);
+        per_sm = nb > 0 ? nb : 1;
+    }
+    return sms * per_sm;
+}
+
 }  // namespace
+
+long long max_segments_per_ray(const Geom& g, int seg_len) {
+    const int n = g.nx > g.ny ? (g.nx > g.nz ? g.nx : g.nz) : (g.ny > g.nz ? g.ny : g.nz);
+    return (n + seg_len - 1) / seg_len;
+}
 
 cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st) {
     const int block = 256;
@@ -289,11 +544,17 @@ cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d
     return cudaGetLastError();
 }
 
-cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t st) {
+cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    const long long blocks = (a.n + kIngestBlock - 1) / kIngestBlock;
+    cudaError_t e = cudaMemsetAsync(a.w.item_count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (a.n + kRaysBlock - 1) / kRaysBlock;
     count_launch();
-    k_ingest<<<(unsigned)blocks, kIngestBlock, 0, st>>>(a);
+    k_rays<<<(unsigned)blocks, kRaysBlock, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_march<<<march_grid(shape), shape.block, 0, st>>>(a);
     return cudaGetLastError();
 }
 
