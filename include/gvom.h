@@ -30,7 +30,9 @@
  *    ((ix * ny) + iy) * nz + iz. 2D products are [ix * ny + iy].
  *  - Points are float32 xyz in the sensor frame, `stride` floats apart (3
  *    for packed xyz, 4 for xyz + padding/intensity).
- *  - T_ws is the row-major 3x4 world-from-sensor transform [R | t], FP64.
+ *  - T_ws is the row-major 3x4 world-from-sensor transform [R | t], FP64,
+ *    finite, with every entry of the rotation part R in [-1, 1] (a rotation;
+ *    1e-6 of rounding slack); other poses are rejected as invalid arguments.
  */
 #ifndef GVOM_H
 #define GVOM_H
@@ -62,7 +64,7 @@ typedef enum gvom_status {
 /* Map parameters (Sec. III-A map size and resolution; Sec. III-D obstacle,
  * slope and negative obstacle parameters, which the paper leaves unnamed).
  * Limits: 1 <= nx, ny, nz <= 4096 with nx * ny * nz < 2^31; res > 0;
- * 0 < max_range with max_range / res < 2^20; 0 <= obs_min_h <= obs_max_h;
+ * 0 < max_range with max_range / res <= 8192; 0 <= obs_min_h <= obs_max_h;
  * 0 < hard_den <= 65535, hard_num <= hard_den; slope_n odd in [3, 15];
  * 3 <= slope_min_px <= slope_n^2; 1 <= neg_max_px <= 64. */
 typedef struct gvom_config {

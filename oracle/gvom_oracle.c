@@ -10,7 +10,8 @@
  * Every function follows the paper (G-VOM, Overbye & Saripalli, arXiv
  * 2109.13176) section it cites; where the paper is silent the reading used is
  * stated next to the code. Build with -ffp-contract=off: every FP64 operation
- * below is one IEEE round-to-nearest operation, in the order written.
+ * below is one IEEE round-to-nearest operation, in the order written, and
+ * fma() is the correctly rounded fused multiply-add of C99.
  *
  * State layout (logical, window-relative, un-rotated):
  *   cell (ix, iy, iz), 0 <= ix < nx ..., linear index ((ix*ny)+iy)*nz+iz
@@ -268,11 +269,12 @@ static void pass_visit(void* vctx, const int64_t cell[3])
 
 /* Quantise a map-frame coordinate to 1/256 voxel relative to the origin.
  * Returns 0 if it is beyond the representable range. Reading: endpoints at
- * 1/256 voxel, v = w/res - O, q = round-half-even(256 v). */
-static int quantise(double w, double inv_res, int64_t origin, int64_t* q)
+ * 1/256 voxel, q = round-half-even(256 (w/res - O)), evaluated as one fused
+ * multiply-add s = fma(w, S, -256 O) with S = 256 * (1/res) (both scalings
+ * by 256 are exact). */
+static int quantise(double w, double S, int64_t origin, int64_t* q)
 {
-    const double v = w * inv_res - (double)origin;
-    const double s = v * 256.0;
+    const double s = fma(w, S, -256.0 * (double)origin);
     if (!(fabs(s) < (double)OR_QLIM)) return 0;
     *q = llrint(s);
     return 1;
@@ -281,10 +283,12 @@ static int quantise(double w, double inv_res, int64_t origin, int64_t* q)
 /* Per-scan update (Sec. III-C pointcloud processing, combined per Sec. III-D).
  *
  * 1. Transform (Sec. III-C): w = R p + t with T = [R | t] row-major 3x4,
- *    w_i = ((T_i0 px + T_i1 py) + T_i2 pz) + T_i3, FP64, no fused ops.
+ *    w_i = fma(T_i2, pz, fma(T_i1, py, fma(T_i0, px, T_i3))) in FP64 (each
+ *    fused multiply-add rounded once, in this order).
  *    The sensor origin is o = (T_03, T_13, T_23).
  * 2. Filter (reading): keep a point iff its components are finite and
- *    0 < px^2 + py^2 + pz^2 <= max_range^2 in the sensor frame.
+ *    0 < r2 <= max_range^2 in the sensor frame, with
+ *    r2 = fma(pz, pz, fma(py, py, px * px)) in FP64.
  * 3. Quantise sensor and endpoint (reading, above).
  * 4. Hits and lowest return (Sec. III-A): the endpoint cell, if in the
  *    window, gains one hit and min height min(minz, (float) w_z).
@@ -302,28 +306,28 @@ void or_ingest(const or_params* p, const int64_t origin[3], uint32_t* hits, uint
                float* minz, const float* pts, int64_t n, int32_t stride, const double T[12],
                or_stats* st)
 {
-    const double inv_res = 1.0 / p->res;
+    const double S = 256.0 * (1.0 / p->res);
     const double r2max = p->max_range * p->max_range;
     int64_t qo[3];
     int sensor_ok = 1;
     for (int a = 0; a < 3; ++a)
-        if (!quantise(T[4 * a + 3], inv_res, origin[a], &qo[a])) sensor_ok = 0;
+        if (!quantise(T[4 * a + 3], S, origin[a], &qo[a])) sensor_ok = 0;
 
     for (int64_t i = 0; i < n; ++i) {
         st->points_in += 1;
         const float fx = pts[i * stride + 0], fy = pts[i * stride + 1], fz = pts[i * stride + 2];
         if (!isfinite(fx) || !isfinite(fy) || !isfinite(fz)) continue;
         const double px = (double)fx, py = (double)fy, pz = (double)fz;
-        const double r2 = (px * px + py * py) + pz * pz;
+        const double r2 = fma(pz, pz, fma(py, py, px * px));
         if (!(r2 > 0.0 && r2 <= r2max)) continue;
         if (!sensor_ok) continue;
         double w[3];
         for (int a = 0; a < 3; ++a)
-            w[a] = ((T[4 * a + 0] * px + T[4 * a + 1] * py) + T[4 * a + 2] * pz) + T[4 * a + 3];
+            w[a] = fma(T[4 * a + 2], pz, fma(T[4 * a + 1], py, fma(T[4 * a + 0], px, T[4 * a + 3])));
         int64_t q[3];
         int ok = 1;
         for (int a = 0; a < 3; ++a)
-            if (!quantise(w[a], inv_res, origin[a], &q[a])) ok = 0;
+            if (!quantise(w[a], S, origin[a], &q[a])) ok = 0;
         if (!ok) continue;
         st->rays_valid += 1;
 

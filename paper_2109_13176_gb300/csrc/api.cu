@@ -42,7 +42,7 @@ bool valid_config(const gvom_config* c) {
     if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return false;
     if (c->reserved0 != 0) return false;
     if (!(c->res > 0.0) || !isfinite(c->res)) return false;
-    if (!(c->max_range > 0.0) || !isfinite(c->max_range) || !(c->max_range / c->res < 1048576.0)) return false;
+    if (!(c->max_range > 0.0) || !isfinite(c->max_range) || !(c->max_range / c->res <= 8192.0)) return false;
     if (!(c->obs_min_h >= 0.0f) || !(c->obs_max_h >= c->obs_min_h) || !isfinite(c->obs_max_h)) return false;
     if (c->hard_den == 0 || c->hard_den > 65535u || c->hard_num > c->hard_den) return false;
     if (c->slope_n < 3 || c->slope_n > 15 || (c->slope_n % 2) == 0) return false;
@@ -97,6 +97,18 @@ ExtractParams extract_params(const gvom_map* m) {
     p.neg_max_px = m->cfg.neg_max_px;
     p.neg_thresh = m->cfg.neg_thresh;
     return p;
+}
+
+// A pose must be finite with a rotation part whose entries lie in [-1, 1]
+// (up to rounding), so that no ray is longer than sqrt(3) max_range in the
+// map frame; the traversal's 32-bit arithmetic relies on that bound.
+bool valid_pose(const double T[12]) {
+    for (int k = 0; k < 12; ++k)
+        if (!isfinite(T[k])) return false;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            if (fabs(T[4 * r + c]) > 1.0 + 1e-6) return false;
+    return true;
 }
 
 bool valid_tuning(const gvom_tuning* t) {
@@ -285,8 +297,7 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     if (n > GVOM_MAX_SCAN_POINTS) return GVOM_ERR_INVALID_ARG;
     if (stride == 4 && (((uintptr_t)pts_dev) & 15u) != 0) return GVOM_ERR_INVALID_ARG;
     if ((((uintptr_t)pts_dev) & 3u) != 0) return GVOM_ERR_INVALID_ARG;
-    for (int k = 0; k < 12; ++k)
-        if (!isfinite(T_ws[k])) return GVOM_ERR_INVALID_ARG;
+    if (!valid_pose(T_ws)) return GVOM_ERR_INVALID_ARG;
     if (n == 0) {
         m->scans += 1;
         return GVOM_OK;
@@ -299,9 +310,9 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     a.n = n;
     a.stride = stride;
     for (int k = 0; k < 12; ++k) a.T[k] = T_ws[k];
-    a.inv_res = 1.0 / m->cfg.res;
+    a.S = 256.0 * (1.0 / m->cfg.res);
     a.r2max = m->cfg.max_range * m->cfg.max_range;
-    for (int k = 0; k < 3; ++k) a.origin[k] = m->origin[k];
+    for (int k = 0; k < 3; ++k) a.neg_o256[k] = -256.0 * (double)m->origin[k];
     a.g = geom_of(m);
     a.s = m->s;
     a.w = m->w;
@@ -318,8 +329,7 @@ int gvom_update(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, 
                 const double T_ws[12], gvom_stream_t stream) {
     if (!m || !vehicle_xyz || !T_ws || n < 0 || (stride != 3 && stride != 4) || (n > 0 && !pts_dev))
         return GVOM_ERR_INVALID_ARG;
-    for (int k = 0; k < 12; ++k)
-        if (!isfinite(T_ws[k])) return GVOM_ERR_INVALID_ARG;
+    if (!valid_pose(T_ws)) return GVOM_ERR_INVALID_ARG;
     int64_t o[3];
     int rc = gvom_origin_for_pose(m, vehicle_xyz, o);
     if (rc != GVOM_OK) return rc;

@@ -1,13 +1,18 @@
 // 2D products of the voxel map (G-VOM Sec. III-D) for sm_103a.
 //
-// k_columns: one warp per map column streams the column's hits, passes and
-// lowest-return heights (contiguous in memory: z is the fastest axis) and
-// reduces them with warp shuffles into the height, the positive obstacle
-// band sums, density and hard/soft flags.
-// k_slope_negative: one thread per pixel over the height map. A defined
-// pixel gets the N x N least-squares plane (slope, roughness); an
-// undefined one runs the four-cone negative obstacle search. The two are
-// exclusive per pixel, so one launch covers both.
+// k_columns: the column pass. A map column is three contiguous runs of nz
+// words (hits, passes, lowest returns; z is the fastest axis), so a group
+// of lanes streams each run with 16-byte loads and reduces it with
+// shuffles into the height, the positive obstacle band sums, density and
+// hard/soft flags. Bandwidth-bound: 12 bytes read per voxel.
+// k_slope_negative: the pixel pass, one 16 x 16 tile of the height map per
+// block, staged in shared memory with a halo. Defined pixels get the N x N
+// least-squares plane (slope, roughness). Undefined pixels get the four-cone
+// negative obstacle search, computed for the whole tile at once by a sweep
+// per cone direction: the cone of a pixel at ring d is the union of the
+// cones of its three forward neighbours at ring d - 1, so each pixel's
+// first ring holding ground, and the lowest height on it, follow from the
+// neighbours' in O(1).
 #include <math.h>
 
 #include "gvom_internal.h"
@@ -18,8 +23,43 @@ namespace {
 
 constexpr int kColBlock = 256;
 
-__global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams p, float* __restrict__ height,
-                                                        float* __restrict__ density, uint8_t* __restrict__ flags) {
+// density = (float)((double)H / (double)(H + M)), the oracle's FP64
+// division rounded to float. When H + M < 2^24 both operands are exact
+// floats and the quotient's distance to any float rounding midpoint is at
+// least 2^-24 of a float ulp, far above the FP64 rounding error, so the
+// correctly rounded FP32 division gives the same float; otherwise FP64.
+__device__ __forceinline__ float density_of(unsigned long long H, unsigned long long D) {
+    if (D < (1ull << 24)) return __fdiv_rn((float)(unsigned int)H, (float)(unsigned int)D);
+    return __double2float_rn(__ddiv_rn((double)H, (double)D));
+}
+
+// The oracle's test lo <= (double)a - (double)b <= hi for floats a, b and
+// float bounds: decided on the FP32 difference unless that lies within a
+// relative 2^-20 of a bound (where FP32 and FP64 rounding could disagree),
+// and there by the FP64 difference.
+__device__ __forceinline__ bool in_band(float a, float b, float lo, float hi) {
+    const float d = __fsub_rn(a, b);
+    const float tl = fabsf(lo) * 9.5367432e-7f + 1e-30f;
+    const float th = fabsf(hi) * 9.5367432e-7f + 1e-30f;
+    if (fabsf(d - lo) <= tl || fabsf(d - hi) <= th) {
+        const double e = __dsub_rn((double)a, (double)b);
+        return (double)lo <= e && e <= (double)hi;
+    }
+    return lo <= d && d <= hi;
+}
+
+// The oracle's test (double)hi - (double)lo > thresh, filtered the same way.
+__device__ __forceinline__ bool exceeds(float hi, float lo, float thresh) {
+    const float d = __fsub_rn(hi, lo);
+    if (fabsf(d - thresh) <= fabsf(thresh) * 9.5367432e-7f + 1e-30f)
+        return __dsub_rn((double)hi, (double)lo) > (double)thresh;
+    return d > thresh;
+}
+
+// Scalar column pass for any nz: one warp per column.
+__global__ void __launch_bounds__(kColBlock) k_columns_scalar(MapState s, ExtractParams p, float* __restrict__ height,
+                                                               float* __restrict__ density,
+                                                               uint8_t* __restrict__ flags) {
     const Geom g = p.g;
     const long long col = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -50,13 +90,10 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
 
     unsigned long long H = 0, M = 0;
     if (any) {
-        const double hd = (double)h;
-        const double lo = (double)p.obs_min_h, hi = (double)p.obs_max_h;
         for (int z = lane; z < g.nz; z += 32) {
             const uint32_t nh = hc[z];
             if (nh == 0u) continue;
-            const double above = __dsub_rn((double)mc[z], hd);
-            if (lo <= above && above <= hi) {
+            if (in_band(mc[z], h, p.obs_min_h, p.obs_max_h)) {
                 H += nh;
                 M += pc[z];
             }
@@ -73,7 +110,7 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
         uint8_t f = 0;
         float dens = 0.0f;
         if (H > 0) {
-            dens = __double2float_rn(__ddiv_rn((double)H, (double)(H + M)));
+            dens = density_of(H, H + M);
             const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
             f = hard ? 3 : 5;
         }
@@ -82,114 +119,324 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
     }
 }
 
-constexpr int kPxBlockX = 32, kPxBlockY = 8;
+// Vector column pass for nz % 4 == 0: LPC lanes per column, each lane
+// loading 16 bytes (4 voxels) per run and step, a grid-stride loop over
+// column groups.
+template <int LPC>
+__global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams p, float* __restrict__ height,
+                                                        float* __restrict__ density, uint8_t* __restrict__ flags) {
+    const Geom g = p.g;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LPC;                  // lane within the column group
+    const unsigned gmask = (LPC == 32) ? 0xffffffffu : (((1u << LPC) - 1u) << (lane - sub));
+    const long long ncols = (long long)g.nx * g.ny;
+    const long long groups_per_warp = 32 / LPC;
+    const long long gtid = (long long)blockIdx.x * kColBlock + threadIdx.x;
+    const long long col0 = (gtid >> 5) * groups_per_warp + (lane / LPC);
+    const long long cstride = (((long long)gridDim.x * kColBlock) >> 5) * groups_per_warp;
+    const int nv = g.nz >> 2;  // 16-byte vectors per run
+    const float lof = p.obs_min_h, hif = p.obs_max_h;
 
-__global__ void __launch_bounds__(kPxBlockX* kPxBlockY)
+    for (long long colb = col0 - (lane / LPC); colb < ncols; colb += cstride) {
+        const long long col = colb + (lane / LPC);
+        const bool have = col < ncols;
+        int cx = 0, cy = 0;
+        size_t base = 0;
+        if (have) {
+            cx = (int)(col / g.ny);
+            cy = (int)(col % g.ny);
+            int px = cx + g.rx;
+            px -= (px >= g.nx) ? g.nx : 0;
+            int py = cy + g.ry;
+            py -= (py >= g.ny) ? g.ny : 0;
+            base = ((size_t)px * g.ny + py) * (size_t)g.nz;
+        }
+        const uint4* hc = reinterpret_cast<const uint4*>(s.hits + base);
+        const float4* mc = reinterpret_cast<const float4*>(s.minz + base);
+        float h = __int_as_float(0x7f800000);
+        bool any = false;
+        if (have) {
+            for (int v = sub; v < nv; v += LPC) {
+                const uint4 hv = __ldg(hc + v);
+                const float4 mv = __ldg(mc + v);
+                if (hv.x) { h = fminf(h, mv.x); any = true; }
+                if (hv.y) { h = fminf(h, mv.y); any = true; }
+                if (hv.z) { h = fminf(h, mv.z); any = true; }
+                if (hv.w) { h = fminf(h, mv.w); any = true; }
+            }
+        }
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
+        const bool col_any = (__ballot_sync(0xffffffffu, any) & gmask) != 0u;
+
+        // Obstacle band: hits and passes summed over occupied voxels whose
+        // lowest return lies in [h + obs_min_h, h + obs_max_h] (FP64
+        // difference of the two floats, like the oracle).
+        unsigned long long H = 0, M = 0;
+        bool inband = false;
+        if (have && col_any) {
+            const uint4* pcv = reinterpret_cast<const uint4*>(s.passes + base);
+            for (int v = sub; v < nv; v += LPC) {
+                const uint4 hv = __ldg(hc + v);
+                const float4 mv = __ldg(mc + v);
+                const uint32_t hs[4] = {hv.x, hv.y, hv.z, hv.w};
+                const float ms[4] = {mv.x, mv.y, mv.z, mv.w};
+                bool need = false;
+                bool in[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    in[k] = hs[k] != 0u && in_band(ms[k], h, lof, hif);
+                    need |= in[k];
+                }
+                if (need) {
+                    const uint4 pv = __ldg(pcv + v);
+                    const uint32_t ps[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        if (in[k]) {
+                            H += hs[k];
+                            M += ps[k];
+                        }
+                    inband = true;
+                }
+            }
+        }
+        if (__ballot_sync(0xffffffffu, inband)) {  // warp-uniform: offsets stay inside a group
+#pragma unroll
+            for (int o = LPC / 2; o > 0; o >>= 1) {
+                H += __shfl_xor_sync(0xffffffffu, H, o);
+                M += __shfl_xor_sync(0xffffffffu, M, o);
+            }
+        }
+        if (have && sub == 0) {
+            const size_t o = (size_t)cx * g.ny + cy;
+            if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
+            uint8_t f = 0;
+            float dens = 0.0f;
+            if (H > 0) {
+                dens = density_of(H, H + M);
+                const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
+                f = hard ? 3 : 5;
+            }
+            if (density) density[o] = dens;
+            if (flags) flags[o] = f;
+        }
+    }
+}
+
+constexpr int kTile = 16;
+constexpr int kPxBlock = 256;        // four cone-sweep warps and four plane-fit warps
+constexpr unsigned char kFar = 255;  // no ground within reach
+
+// One warp sweeps the cone recurrence of one direction over the tile. The
+// cone grows along +u (sgn = +1) or -u (sgn = -1), u = the tile's row axis
+// (x) when along_x, else its column axis (y). Ring 1 of a cell is the three
+// cells one step ahead; a cell with no ground on ring 1 takes 1 + the
+// smallest first-ring distance of those three cells, and the lowest height
+// among the ones at that distance. A cone whose ring leaves the grid along
+// u, or whose distance passes neg_max_px, has no value (kFar).
+// Writes the cone value of each tile-interior pixel to val (NaN: none).
+__device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int gx0, int gy0, bool along_x,
+                                int sgn, unsigned char* Dbuf, float* Vbuf, float* val) {
+    const int lane = threadIdx.x & 31;
+    const int nmaj = along_x ? p.g.nx : p.g.ny;
+    const int g0 = along_x ? gx0 : gy0;  // global coordinate of tile row 0 along u
+    const int first = sgn > 0 ? W - 1 : 0;
+    const int last = sgn > 0 ? R : R + kTile - 1;
+    const int nsteps = sgn > 0 ? first - last + 1 : last - first + 1;
+    const float qnan = __int_as_float(0x7fffffff);
+    for (int st = 0; st < nsteps; ++st) {
+        const int u = first - sgn * st;
+        unsigned char* Dcur = Dbuf + (st & 1) * W;
+        float* Vcur = Vbuf + (st & 1) * W;
+        const unsigned char* Dprev = Dbuf + ((st + 1) & 1) * W;
+        const float* Vprev = Vbuf + ((st + 1) & 1) * W;
+        const int un = u + sgn;   // the ring-1 line
+        const int gun = g0 + un;  // its global coordinate
+        const bool ring_ok = gun >= 0 && gun < nmaj && un >= 0 && un < W;
+        for (int v = lane; v < W; v += 32) {
+            unsigned char D = kFar;
+            float V = 0.f;
+            if (ring_ok) {
+                float m = __int_as_float(0x7f800000);
+                bool any = false;
+#pragma unroll
+                for (int dv = -1; dv <= 1; ++dv) {
+                    const int vv = v + dv;
+                    if (vv < 0 || vv >= W) continue;
+                    const float hv = along_x ? Hs[un * W + vv] : Hs[vv * W + un];
+                    if (!isnan(hv)) {
+                        m = fminf(m, hv);
+                        any = true;
+                    }
+                }
+                if (any) {
+                    D = 1;
+                    V = m;
+                } else if (st > 0) {
+                    unsigned char dmin = kFar;
+                    float mv = __int_as_float(0x7f800000);
+#pragma unroll
+                    for (int dv = -1; dv <= 1; ++dv) {
+                        const int vv = v + dv;
+                        if (vv < 0 || vv >= W) continue;
+                        const unsigned char dd = Dprev[vv];
+                        const float vvv = Vprev[vv];
+                        if (dd < dmin) {
+                            dmin = dd;
+                            mv = vvv;
+                        } else if (dd == dmin) {
+                            mv = fminf(mv, vvv);
+                        }
+                    }
+                    if (dmin != kFar && (int)dmin + 1 <= p.neg_max_px) {
+                        D = (unsigned char)(dmin + 1);
+                        V = mv;
+                    }
+                }
+            }
+            Dcur[v] = D;
+            Vcur[v] = V;
+            const int iu = u - R, iv = v - R;
+            if (iu >= 0 && iu < kTile && iv >= 0 && iv < kTile)
+                val[along_x ? iu * kTile + iv : iv * kTile + iu] = D != kFar ? V : qnan;
+        }
+        __syncwarp();
+    }
+}
+
+// Least-squares plane z = a i + b j + c over the defined pixels of the
+// (2r+1)^2 window around tile cell (ci, cj), z relative to the centre
+// height h0. The normal matrix is integer (exact, so is the singularity
+// test); the right-hand side and the solve are FP32.
+template <int kR>
+__device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* Hs, int W, int ci, int cj, float h0,
+                                          float& sl, float& ro) {
+    // kR > 0: compile-time radius (loops unrolled); kR == 0: run-time radius
+    const int r = kR > 0 ? kR : p.slope_n / 2;
+    int n = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+    float sz = 0.f, siz = 0.f, sjz = 0.f;
+#pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
+    for (int i = -r; i <= r; ++i)
+#pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
+        for (int j = -r; j <= r; ++j) {
+            const float hv = Hs[(ci + i) * W + (cj + j)];
+            if (isnan(hv)) continue;
+            const float z = hv - h0;
+            n += 1;
+            si += i;
+            sj += j;
+            sii += i * i;
+            sjj += j * j;
+            sij += i * j;
+            sz += z;
+            siz += (float)i * z;
+            sjz += (float)j * z;
+        }
+    // adjugate of [sii sij si; sij sjj sj; si sj n] (symmetric)
+    const long long A00 = (long long)sjj * n - (long long)sj * sj;
+    const long long A01 = -((long long)sij * n - (long long)sj * si);
+    const long long A02 = (long long)sij * sj - (long long)sjj * si;
+    const long long A11 = (long long)sii * n - (long long)si * si;
+    const long long A12 = -((long long)sii * sj - (long long)sij * si);
+    const long long A22 = (long long)sii * sjj - (long long)sij * sij;
+    const long long det = (long long)sii * A00 + (long long)sij * A01 + (long long)si * A02;
+    if (n < p.slope_min_px || det == 0) return;
+    const float inv = 1.0f / (float)det;
+    const float a = ((float)A00 * siz + (float)A01 * sjz + (float)A02 * sz) * inv;
+    const float b = ((float)A01 * siz + (float)A11 * sjz + (float)A12 * sz) * inv;
+    const float c = ((float)A02 * siz + (float)A12 * sjz + (float)A22 * sz) * inv;
+    float sse = 0.f;
+#pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
+    for (int i = -r; i <= r; ++i)
+#pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
+        for (int j = -r; j <= r; ++j) {
+            const float hv = Hs[(ci + i) * W + (cj + j)];
+            if (isnan(hv)) continue;
+            const float e = (hv - h0) - (a * (float)i + b * (float)j + c);
+            sse += e * e;
+        }
+    sl = atanf(hypotf(a, b) / p.res);
+    ro = sse / (float)n;
+}
+
+// Block: warps 0-3 sweep the four cones (+x, -x, +y, -y) while warps 4-7
+// fit the planes of the defined pixels; then every thread combines the
+// cone values of one pixel.
+__global__ void __launch_bounds__(kPxBlock, 4)
     k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
                      float* __restrict__ rough, uint8_t* __restrict__ flags) {
+    extern __shared__ float smem[];
     const int nx = p.g.nx, ny = p.g.ny;
-    const int cy = blockIdx.x * kPxBlockX + threadIdx.x;
-    const int cx = blockIdx.y * kPxBlockY + threadIdx.y;
-    if (cx >= nx || cy >= ny) return;
-    const size_t o = (size_t)cx * ny + cy;
-    const float h0 = height[o];
+    const int r = p.slope_n / 2;
+    const int R = max(p.neg_max_px, r);
+    const int W = kTile + 2 * R;
+    const int warp = threadIdx.x >> 5;
+    float* Hs = smem;                                   // W * W heights, NaN outside the grid
+    float* vals = Hs + W * W;                           // 4 * kTile^2 cone values
+    float* Vbufs = vals + 4 * kTile * kTile;            // 4 * 2W
+    unsigned char* Dbufs = reinterpret_cast<unsigned char*>(Vbufs + 8 * W);  // 4 * 2W
+    const int tx0 = blockIdx.y * kTile, ty0 = blockIdx.x * kTile;
+    const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
 
-    if (!isnan(h0)) {
-        // Least-squares plane z = a i + b j + c over the defined pixels of
-        // the N x N window, z relative to the centre height. The normal
-        // matrix is integer (exact); the right-hand side is FP32.
-        const int r = p.slope_n / 2;
-        int n = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
-        float sz = 0.f, siz = 0.f, sjz = 0.f;
-        for (int i = -r; i <= r; ++i) {
-            const int x = cx + i;
-            if (x < 0 || x >= nx) continue;
-            for (int j = -r; j <= r; ++j) {
-                const int y = cy + j;
-                if (y < 0 || y >= ny) continue;
-                const float hv = height[(size_t)x * ny + y];
-                if (isnan(hv)) continue;
-                const float z = hv - h0;
-                n += 1;
-                si += i;
-                sj += j;
-                sii += i * i;
-                sjj += j * j;
-                sij += i * j;
-                sz += z;
-                siz += (float)i * z;
-                sjz += (float)j * z;
-            }
-        }
-        float sl = qnan, ro = qnan;
-        // adjugate of [sii sij si; sij sjj sj; si sj n] (symmetric)
-        const long long A00 = (long long)sjj * n - (long long)sj * sj;
-        const long long A01 = -((long long)sij * n - (long long)sj * si);
-        const long long A02 = (long long)sij * sj - (long long)sjj * si;
-        const long long A11 = (long long)sii * n - (long long)si * si;
-        const long long A12 = -((long long)sii * sj - (long long)sij * si);
-        const long long A22 = (long long)sii * sjj - (long long)sij * sij;
-        const long long det = (long long)sii * A00 + (long long)sij * A01 + (long long)si * A02;
-        if (n >= p.slope_min_px && det != 0) {
-            const float inv = 1.0f / (float)det;
-            const float a = ((float)A00 * siz + (float)A01 * sjz + (float)A02 * sz) * inv;
-            const float b = ((float)A01 * siz + (float)A11 * sjz + (float)A12 * sz) * inv;
-            const float c = ((float)A02 * siz + (float)A12 * sjz + (float)A22 * sz) * inv;
-            float sse = 0.f;
-            for (int i = -r; i <= r; ++i) {
-                const int x = cx + i;
-                if (x < 0 || x >= nx) continue;
-                for (int j = -r; j <= r; ++j) {
-                    const int y = cy + j;
-                    if (y < 0 || y >= ny) continue;
-                    const float hv = height[(size_t)x * ny + y];
-                    if (isnan(hv)) continue;
-                    const float e = (hv - h0) - (a * (float)i + b * (float)j + c);
-                    sse += e * e;
-                }
-            }
-            sl = atanf(hypotf(a, b) / p.res);
-            ro = sse / (float)n;
-        }
-        if (slope) slope[o] = sl;
-        if (rough) rough[o] = ro;
-        return;
+    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
+        const int i = t / W, j = t % W;
+        const int gx = gx0 + i, gy = gy0 + j;
+        Hs[t] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
     }
+    __syncthreads();
 
-    if (slope) slope[o] = qnan;
-    if (rough) rough[o] = qnan;
-    // Negative obstacle search: four cones (+x, -x, +y, -y), ring by ring.
-    int nfound = 0;
-    float lo = 0.f, hi = 0.f;
-#pragma unroll 1
-    for (int cone = 0; cone < 4; ++cone) {
-        const int ax = cone < 2 ? 1 : 0;  // 1: the ring is a fixed x
-        const int sgn = (cone & 1) ? -1 : 1;
-        for (int d = 1; d <= p.neg_max_px; ++d) {
-            const int fixed = (ax ? cx : cy) + sgn * d;
-            if (fixed < 0 || fixed >= (ax ? nx : ny)) break;
-            const int centre = ax ? cy : cx;
-            const int lim = ax ? ny : nx;
-            const int s0 = max(centre - d, 0), s1 = min(centre + d, lim - 1);
-            float best = __int_as_float(0x7f800000);
-            bool found = false;
-            for (int s = s0; s <= s1; ++s) {
-                const float hv = ax ? height[(size_t)fixed * ny + s] : height[(size_t)s * ny + fixed];
-                if (!isnan(hv)) {
-                    best = fminf(best, hv);
-                    found = true;
-                }
+    if (warp < 4) {
+        if (flags)
+            cone_sweep_warp(p, Hs, W, R, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Dbufs + warp * 2 * W,
+                            Vbufs + warp * 2 * W, vals + warp * kTile * kTile);
+    } else {
+        for (int t = threadIdx.x - 128; t < kTile * kTile; t += 128) {
+            const int li = t / kTile, lj = t % kTile;
+            const int cx = tx0 + li, cy = ty0 + lj;
+            if (cx >= nx || cy >= ny) continue;
+            const int ci = li + R, cj = lj + R;
+            const float h0 = Hs[ci * W + cj];
+            float sl = qnan, ro = qnan;
+            if (!isnan(h0)) {
+                if (r == 2)
+                    plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
+                else if (r == 1)
+                    plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
+                else
+                    plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
             }
-            if (found) {
-                lo = nfound ? fminf(lo, best) : best;
-                hi = nfound ? fmaxf(hi, best) : best;
-                nfound += 1;
-                break;
-            }
+            const size_t o = (size_t)cx * ny + cy;
+            if (slope) slope[o] = sl;
+            if (rough) rough[o] = ro;
         }
     }
-    if (flags && nfound >= 2 && __dsub_rn((double)hi, (double)lo) > (double)p.neg_thresh) flags[o] |= 8u;
+    if (!flags) return;
+    __syncthreads();
+    for (int t = threadIdx.x; t < kTile * kTile; t += blockDim.x) {
+        const int li = t / kTile, lj = t % kTile;
+        const int cx = tx0 + li, cy = ty0 + lj;
+        if (cx >= nx || cy >= ny) continue;
+        if (!isnan(Hs[(li + R) * W + (lj + R)])) continue;
+        int nf = 0;
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float v = vals[c * kTile * kTile + t];
+            if (isnan(v)) continue;
+            lo = nf ? fminf(lo, v) : v;
+            hi = nf ? fmaxf(hi, v) : v;
+            nf += 1;
+        }
+        if (nf >= 2 && exceeds(hi, lo, p.neg_thresh)) flags[(size_t)cx * ny + cy] |= 8u;
+    }
+}
+
+size_t slope_negative_smem(const ExtractParams& p) {
+    const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
+    const int W = kTile + 2 * R;
+    return sizeof(float) * ((size_t)W * W + 4 * kTile * kTile + 8 * (size_t)W) + 8 * (size_t)W;
 }
 
 __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits, uint32_t* __restrict__ passes,
@@ -213,23 +460,50 @@ __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits,
     }
 }
 
+int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
 }  // namespace
 
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density, uint8_t* flags,
                            cudaStream_t st) {
     const long long cols = (long long)p.g.nx * p.g.ny;
-    const long long blocks = (cols * 32 + kColBlock - 1) / kColBlock;
     count_launch();
-    k_columns<<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
+    if ((p.g.nz & 3) != 0) {
+        const long long blocks = (cols * 32 + kColBlock - 1) / kColBlock;
+        k_columns_scalar<<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
+        return cudaGetLastError();
+    }
+    const int nv = p.g.nz / 4;
+    const int lpc = nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
+    const long long groups = (cols + (32 / lpc) - 1) / (32 / lpc);  // warps needed for one column each
+    long long blocks = (groups * 32 + kColBlock - 1) / kColBlock;
+    const long long cap = (long long)sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    if (lpc == 8)
+        k_columns<8><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
+    else if (lpc == 16)
+        k_columns<16><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
+    else
+        k_columns<32><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
     return cudaGetLastError();
 }
 
 cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, float* slope, float* rough,
                                   uint8_t* flags, cudaStream_t st) {
-    dim3 block(kPxBlockX, kPxBlockY);
-    dim3 grid((p.g.ny + kPxBlockX - 1) / kPxBlockX, (p.g.nx + kPxBlockY - 1) / kPxBlockY);
+    const size_t smem = slope_negative_smem(p);
+    if (smem > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_slope_negative, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((p.g.ny + kTile - 1) / kTile, (p.g.nx + kTile - 1) / kTile);
     count_launch();
-    k_slope_negative<<<grid, block, 0, st>>>(p, height, slope, rough, flags);
+    k_slope_negative<<<grid, kPxBlock, smem, st>>>(p, height, slope, rough, flags);
     return cudaGetLastError();
 }
 

@@ -46,9 +46,9 @@ struct IngestArgs {
     int stride;
     int seg_len;              // major-axis voxel slabs per traversal segment
     double T[12];
-    double inv_res;
+    double S;            // 256 * (1 / res): 1/256-voxel units per metre
+    double neg_o256[3];  // -256 * origin (exact)
     double r2max;
-    long long origin[3];
     Geom g;
     MapState s;
     RayScratch w;

@@ -57,19 +57,36 @@ __device__ __forceinline__ void atomic_min_f32(float* addr, float v) {
         atomicMax(reinterpret_cast<unsigned int*>(addr), __float_as_uint(v));
 }
 
-// Sec. III-C transform, one row of [R | t]: ((r0 px + r1 py) + r2 pz) + t,
-// each operation rounded on its own (no FMA contraction).
+// Sec. III-C transform, one row of [R | t]:
+// fma(r2, pz, fma(r1, py, fma(r0, px, t))), each fused multiply-add
+// rounded once, in this order.
 __device__ __forceinline__ double xform_row(const double* T, double px, double py, double pz) {
-    return __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(T[0], px), __dmul_rn(T[1], py)), __dmul_rn(T[2], pz)), T[3]);
+    return __fma_rn(T[2], pz, __fma_rn(T[1], py, __fma_rn(T[0], px, T[3])));
 }
 
-// Quantise a map-frame coordinate: q = round-half-even(256 (w / res - origin)).
-__device__ __forceinline__ bool quantise(double w, double inv_res, long long origin, int* q) {
-    const double v = __dsub_rn(__dmul_rn(w, inv_res), (double)origin);
-    const double s = v * 256.0;  // exact: scaling by a power of two
+// Quantise a map-frame coordinate to 1/256 voxel from the window origin:
+// q = round-half-even(fma(w, S, -256 origin)) with S = 256 (1 / res).
+__device__ __forceinline__ bool quantise(double w, double S, double neg_o256, int* q) {
+    const double s = __fma_rn(w, S, neg_o256);
     if (!(fabs(s) < kQLim)) return false;
     *q = (int)__double2ll_rn(s);
     return true;
+}
+
+// The sensor's quantised position, computed once per block and shared.
+// Returns false (for every thread) when it cannot be quantised.
+__device__ __forceinline__ bool block_sensor(const IngestArgs& a, int qo[3]) {
+    __shared__ int s_q[4];
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) ok &= quantise(a.T[4 * k + 3], a.S, a.neg_o256[k], &s_q[k]);
+        s_q[3] = ok;
+    }
+    __syncthreads();
+    qo[0] = s_q[0];
+    qo[1] = s_q[1];
+    qo[2] = s_q[2];
+    return s_q[3] != 0;
 }
 
 __device__ __forceinline__ int iabs(int v) { return v < 0 ? -v : v; }
@@ -136,9 +153,7 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
     int q[3] = {0, 0, 0};
     float wz = 0.0f;
     int qo[3];
-    bool sensor_ok = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sensor_ok &= quantise(a.T[4 * k + 3], a.inv_res, a.origin[k], &qo[k]);
+    const bool sensor_ok = block_sensor(a, qo);
 
     if (i < a.n) {
         const float* p = a.pts + i * a.stride;
@@ -155,13 +170,13 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
         }
         if (isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok) {
             const double px = fx, py = fy, pz = fz;
-            const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+            const double r2 = __fma_rn(pz, pz, __fma_rn(py, py, __dmul_rn(px, px)));
             if (r2 > 0.0 && r2 <= a.r2max) {
                 const double wx = xform_row(a.T + 0, px, py, pz);
                 const double wy = xform_row(a.T + 4, px, py, pz);
                 const double wzd = xform_row(a.T + 8, px, py, pz);
-                valid = quantise(wx, a.inv_res, a.origin[0], &q[0]) && quantise(wy, a.inv_res, a.origin[1], &q[1]) &&
-                        quantise(wzd, a.inv_res, a.origin[2], &q[2]);
+                valid = quantise(wx, a.S, a.neg_o256[0], &q[0]) && quantise(wy, a.S, a.neg_o256[1], &q[1]) &&
+                        quantise(wzd, a.S, a.neg_o256[2], &q[2]);
                 wz = __double2float_rn(wzd);
             }
         }
@@ -258,10 +273,12 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
 // just after t*) comes with the minor's own crossing at t*, if any, so the
 // voxel is ceil(P / 256) - 1.
 
-// q = floor(x / y) for y > 0 and |x / y| < 2^23: an FP32 estimate corrected
-// exactly with 64-bit integer remainders.
+// q = floor(x / y) for 0 < y < 2^31 and |x / y| < 2^23: an FP32 estimate
+// corrected exactly with 64-bit integer remainders.
 __device__ __forceinline__ long long floor_div_small(long long x, long long y) {
-    long long q = (long long)floorf(__fdiv_rn((float)x, (float)y));
+    // x converted from its two 32-bit halves (FP32 pipe, not the FP64 one)
+    const float xf = fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned int)x);
+    long long q = (long long)floorf(__fdiv_rn(xf, (float)(int)y));
     long long r = x - q * y;
     while (r < 0) {
         q -= 1;
@@ -278,6 +295,7 @@ struct Walk {
     int cM, cA, cB;     // current voxel, window coordinates
     int dirM, dirA, dirB;
     int nA, nB;         // window extents of the minor axes
+    int exitA, exitB;   // the first minor voxel past the window in the walk's direction
     int sM, sA, sB;     // 256 den per axis
     int dMA, dMB, dAB;  // pairwise crossing-time differences
     int tMA, tAM, tMB, tBM, tAB, tBA;  // tie thresholds: i first iff D_ij < t_ij
@@ -363,6 +381,11 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     w.nM = dim_of(g, M);
     w.nA = dim_of(g, A);
     w.nB = dim_of(g, B);
+    w.exitA = dir[1] > 0 ? w.nA : -1;
+    w.exitB = dir[2] > 0 ? w.nB : -1;
+    // a segment that starts with a minor axis already past the window has
+    // nothing left to count
+    if ((dir[1] > 0 ? c[1] >= w.nA : c[1] < 0) || (dir[2] > 0 ? c[2] >= w.nB : c[2] < 0)) return false;
     const int rr[3] = {g.rx, g.ry, g.rz};
     const uint32_t st[3] = {(uint32_t)g.ny * (uint32_t)g.nz, (uint32_t)g.nz, 1u};
     w.rM = sel3(rr, M);
@@ -393,8 +416,7 @@ __global__ void k_march(const IngestArgs a) {
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 
     int qo[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) quantise(a.T[4 * k + 3], a.inv_res, a.origin[k], &qo[k]);
+    block_sensor(a, qo);  // the work list only holds rays of a quantisable sensor
 
     unsigned long long visits = 0;
     for (long long base = gw * 32; base < n_items; base += nwarps * 32) {
@@ -444,10 +466,9 @@ __global__ void k_march(const IngestArgs a) {
             w.dMB += (gM ? w.sB : 0) - (gB ? w.sM : 0);
             w.dAB += (gA ? w.sB : 0) - (gB ? w.sA : 0);
             w.total -= (int)gM + (int)gA + (int)gB;
-            // a minor axis past the window never comes back
-            if ((w.dirA > 0 && w.cA >= w.nA) || (w.dirA < 0 && w.cA < 0) || (w.dirB > 0 && w.cB >= w.nB) ||
-                (w.dirB < 0 && w.cB < 0))
-                live = false;
+            // a minor axis past the window never comes back (steps are unit,
+            // so it passes the window exactly at its exit voxel)
+            if (w.cA == w.exitA || w.cB == w.exitB) live = false;
         }
     }
 
@@ -468,39 +489,59 @@ __global__ void k_init_state(uint32_t* __restrict__ hits, uint32_t* __restrict__
     }
 }
 
-// Clear the voxels that enter the window on a shift by d (new - old origin,
-// |d_k| < n_k on every axis). One warp per window column: a column whose x
-// or y is new is cleared whole; otherwise only its new z range.
-__global__ void k_shift(MapState s, Geom g, int dx, int dy, int dz) {
-    const long long col = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (col >= (long long)g.nx * g.ny) return;
-    const int cx = (int)(col / g.ny), cy = (int)(col % g.ny);
-    const bool new_x = dx > 0 ? cx >= g.nx - dx : cx < -dx;
-    const bool new_y = dy > 0 ? cy >= g.ny - dy : cy < -dy;
-    int z0, z1;
-    if (new_x || new_y) {
-        z0 = 0;
-        z1 = g.nz;
-    } else if (dz > 0) {
-        z0 = g.nz - dz;
-        z1 = g.nz;
-    } else {
-        z0 = 0;
-        z1 = -dz;
-    }
-    if (z0 >= z1) return;
+// Clear the voxels that enter the window on a shift by d = new - old origin
+// (|d_k| < n_k on every axis); g is the new window. The entering voxels are
+// the union of an x slab (|dx| whole columns deep), a y slab (the remaining
+// columns, |dy| deep) and a z slab (|dz| voxels of every remaining column).
+// k_shift_columns clears whole columns, one warp each; k_shift_zslab clears
+// the z slab, one thread per column.
+__device__ __forceinline__ uint32_t column_base(const Geom& g, int cx, int cy) {
     int px = cx + g.rx;
     px -= (px >= g.nx) ? g.nx : 0;
     int py = cy + g.ry;
     py -= (py >= g.ny) ? g.ny : 0;
-    const uint32_t base = ((uint32_t)px * g.ny + py) * (uint32_t)g.nz;
-    for (int cz = z0 + lane; cz < z1; cz += 32) {
+    return ((uint32_t)px * g.ny + py) * (uint32_t)g.nz;
+}
+
+__device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
+    s.hits[k] = 0u;
+    s.passes[k] = 0u;
+    s.minz[k] = __int_as_float(0x7f800000);
+}
+
+__global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_xslab, long long n_units) {
+    const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (u >= n_units) return;
+    const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+    int cx, cy;
+    if (u < n_xslab) {
+        const int k = (int)(u / g.ny);
+        cx = dx > 0 ? g.nx - dx + k : k;
+        cy = (int)(u % g.ny);
+    } else {
+        const long long w = u - n_xslab;
+        const int k = (int)(w / ady), l = (int)(w % ady);
+        cx = (dx > 0 ? 0 : adx) + k;
+        cy = dy > 0 ? g.ny - dy + l : l;
+    }
+    const uint32_t base = column_base(g, cx, cy);
+    for (int cz = lane; cz < g.nz; cz += 32) clear_voxel(s, base + (uint32_t)cz);
+}
+
+__global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
+    const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int wy = g.ny - ady;
+    if (w >= (long long)(g.nx - adx) * wy) return;
+    const int cx = (dx > 0 ? 0 : adx) + (int)(w / wy);
+    const int cy = (dy > 0 ? 0 : ady) + (int)(w % wy);
+    const uint32_t base = column_base(g, cx, cy);
+    const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
+    for (int cz = z0; cz < z1; ++cz) {
         int pz = cz + g.rz;
         pz -= (pz >= g.nz) ? g.nz : 0;
-        s.hits[base + pz] = 0u;
-        s.passes[base + pz] = 0u;
-        s.minz[base + pz] = __int_as_float(0x7f800000);
+        clear_voxel(s, base + (uint32_t)pz);
     }
 }
 
@@ -536,12 +577,28 @@ cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st) {
 }
 
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st) {
-    const long long cols = (long long)g_new.nx * g_new.ny;
-    const int block = 256;
-    const long long blocks = (cols * 32 + block - 1) / block;
-    count_launch();
-    k_shift<<<(unsigned)blocks, block, 0, st>>>(s, g_new, (int)d[0], (int)d[1], (int)d[2]);
-    return cudaGetLastError();
+    const int dx = (int)d[0], dy = (int)d[1], dz = (int)d[2];
+    const long long adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy, adz = dz < 0 ? -dz : dz;
+    const long long n_xslab = adx * g_new.ny;
+    const long long n_cols = n_xslab + (g_new.nx - adx) * ady;
+    if (n_cols > 0) {
+        const int block = 256;
+        const long long blocks = (n_cols * 32 + block - 1) / block;
+        count_launch();
+        k_shift_columns<<<(unsigned)blocks, block, 0, st>>>(s, g_new, dx, dy, n_xslab, n_cols);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (adz > 0) {
+        const long long n = (g_new.nx - adx) * (g_new.ny - ady);
+        if (n > 0) {
+            const int block = 256;
+            count_launch();
+            k_shift_zslab<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(s, g_new, dx, dy, dz);
+            return cudaGetLastError();
+        }
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {

@@ -70,3 +70,10 @@ def test_null_arguments_rejected(lib):
     assert lib.gvom_origin_for_pose(None, None, o) == gv.GVOM_ERR_INVALID_ARG
     assert lib.gvom_config_default(None) == gv.GVOM_ERR_INVALID_ARG
     lib.gvom_destroy(None)  # no-op
+
+
+def test_config_limit_on_range_over_resolution(lib):
+    c = gv.gvom_config_default()
+    c.res, c.max_range = 0.01, 100.0  # 10,000 voxels of range: beyond the 8192 limit
+    h = ctypes.c_void_p()
+    assert lib.gvom_create(ctypes.byref(c), ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG
