@@ -108,7 +108,7 @@ typedef struct gvom_maps_out {
  * and a persistent grid of march_block-thread blocks (march_blocks_per_sm
  * per SM, 0 = as many as fit) walks them. Results do not depend on these;
  * speed does (the autotuner picks them per workload). Limits:
- * 1 <= seg_len <= 4096; march_block in {128, 256, 512};
+ * 1 <= seg_len <= 4096; march_block in {128, 256};
  * 0 <= march_blocks_per_sm <= 32; reserved = 0. */
 typedef struct gvom_tuning {
     int32_t seg_len;
@@ -232,6 +232,46 @@ GVOM_API int gvom_get_stats(struct gvom_map* map, gvom_stats* out);
 
 /* Zeroes the counters. Stream-ordered. */
 GVOM_API int gvom_reset_stats(struct gvom_map* map, gvom_stream_t stream);
+
+/* ---- Batched update of many maps ---------------------------------------
+ * Many independent maps (a fleet, or several sensors each with its own map)
+ * updated together: one step shifts every map to the origin of its vehicle
+ * position, folds one scan into each (exactly what gvom_update does for one
+ * map) and optionally extracts each map's 2D products (exactly what
+ * gvom_extract_maps does). All maps of a step run in a handful of kernels
+ * whose traversal work is balanced across maps of uneven scan size; with
+ * GVOM_BATCH_GRAPH the step is captured once as a CUDA graph and replayed. */
+typedef struct gvom_batch gvom_batch;
+
+#define GVOM_BATCH_GRAPH 1 /* capture the step's kernels in a CUDA graph, replay it */
+
+/* Creates a batch context for steps of up to max_maps maps and max_points
+ * points in total (sum over the maps of one step). Allocates device tables,
+ * the shared per-step scratch (16 bytes per point, plus the segment work
+ * list, grown on demand), two pinned staging buffers and, with
+ * GVOM_BATCH_GRAPH, an internal capture stream. 1 <= max_maps <= 4096. */
+GVOM_API int gvom_batch_create(int32_t max_maps, int64_t max_points, int32_t flags, gvom_batch** out);
+
+/* Frees the context. Synchronises the device. NULL is a no-op. */
+GVOM_API void gvom_batch_destroy(gvom_batch* batch);
+
+/* Traversal tuning for the batch (see gvom_tuning); drops a captured graph. */
+GVOM_API int gvom_batch_set_tuning(gvom_batch* batch, const gvom_tuning* tuning);
+
+/* One step over maps[0 .. B-1] (distinct maps, any configurations, on the
+ * current device): map m shifts to gvom_origin_for_pose(vehicle_xyz + 3m),
+ * ingests n[m] points at pts_dev[m] (stride 3 or 4, alignment as for
+ * gvom_ingest_scan) with pose T_ws + 12m, and, if outs is not NULL, writes
+ * its 2D products to outs[m] (NULL buffers are skipped as in
+ * gvom_extract_maps). Results equal B separate gvom_update +
+ * gvom_extract_maps calls bit for bit. The sum of n[m] must not exceed the
+ * context's max_points. Steps of one context must be issued on one stream
+ * (or ordered by events): the device tables are rewritten each step. The
+ * first step, or one whose shape needs more scratch, waits for `stream`.
+ * Stream-ordered otherwise. Arguments are checked before any map changes. */
+GVOM_API int gvom_batch_step(gvom_batch* batch, struct gvom_map* const* maps, int32_t B, const double* vehicle_xyz,
+                             const float* const* pts_dev, const int64_t* n, int32_t stride, const double* T_ws,
+                             const gvom_maps_out* outs, gvom_stream_t stream);
 
 /* Human-readable name of a status code (static storage). */
 GVOM_API const char* gvom_status_string(int status);

@@ -26,6 +26,7 @@ GVOM_ERR_OUT_OF_MEMORY = -2
 GVOM_ERR_CUDA = -3
 GVOM_ERR_TIMEOUT = -4
 GVOM_ERR_BOUNDS = -5
+GVOM_BATCH_GRAPH = 1
 
 
 class GvomError(RuntimeError):
@@ -111,6 +112,11 @@ def load_library():
             "gvom_set_tuning": ([vp, P(gvom_tuning)], ctypes.c_int),
             "gvom_get_tuning": ([vp, P(gvom_tuning)], ctypes.c_int),
             "gvom_reserve": ([vp, i64, vp], ctypes.c_int),
+            "gvom_batch_create": ([i32, i64, i32, P(vp)], ctypes.c_int),
+            "gvom_batch_destroy": ([vp], None),
+            "gvom_batch_set_tuning": ([vp, P(gvom_tuning)], ctypes.c_int),
+            "gvom_batch_step": ([vp, P(vp), i32, P(ctypes.c_double), P(vp), P(i64), i32, P(ctypes.c_double),
+                                 P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
             "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
@@ -279,6 +285,73 @@ def gvom_get_stats(handle: int) -> dict:
 
 def gvom_reset_stats(handle: int, stream=None) -> None:
     _check(load_library().gvom_reset_stats(handle, _stream_handle(stream)), "gvom_reset_stats")
+
+
+def gvom_batch_create(max_maps: int, max_points: int, flags: int = GVOM_BATCH_GRAPH) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().gvom_batch_create(int(max_maps), int(max_points), int(flags), ctypes.byref(h)),
+           "gvom_batch_create")
+    return h.value
+
+
+def gvom_batch_destroy(handle: int) -> None:
+    load_library().gvom_batch_destroy(handle)
+
+
+def gvom_batch_set_tuning(handle: int, tuning: gvom_tuning) -> None:
+    _check(load_library().gvom_batch_set_tuning(handle, ctypes.byref(tuning)), "gvom_batch_set_tuning")
+
+
+def gvom_batch_step(handle: int, map_handles, vehicle_xyz, points, T_ws, outs=None, stream=None) -> None:
+    """One batched step: map_handles[m] takes the scan points[m] (CUDA float32
+    (n, 3|4) tensors, all the same stride) with pose T_ws[m] at vehicle_xyz[m];
+    outs: None or a list of dicts of output tensors (see VoxelMap.alloc_maps)."""
+    import numpy as np
+    B = len(map_handles)
+    strides = {p.shape[1] for p in points}
+    if len(strides) != 1:
+        raise ValueError("all scans of a step must have the same stride")
+    maps = (ctypes.c_void_p * B)(*map_handles)
+    ptrs, ns = [], []
+    for p in points:
+        ptr, n, _ = _points_args(p)
+        ptrs.append(ptr)
+        ns.append(n)
+    vx = np.ascontiguousarray(vehicle_xyz, dtype=np.float64).reshape(B * 3)
+    T = np.ascontiguousarray(T_ws, dtype=np.float64).reshape(B * 12)
+    c_out = None
+    if outs is not None:
+        c_out = (gvom_maps_out * B)(*[gvom_maps_out(*(o[k].data_ptr() if o.get(k) is not None else None
+                                                        for k in ("height", "density", "flags", "slope", "roughness")))
+                                      for o in outs])
+    _check(load_library().gvom_batch_step(
+        handle, maps, B, (ctypes.c_double * (3 * B))(*vx.tolist()), (ctypes.c_void_p * B)(*ptrs),
+        (ctypes.c_int64 * B)(*ns), strides.pop(), (ctypes.c_double * (12 * B))(*T.tolist()),
+        c_out, _stream_handle(stream)), "gvom_batch_step")
+
+
+class MapBatch:
+    """A batch context: steps many VoxelMaps together (see gvom_batch_step)."""
+
+    def __init__(self, max_maps: int, max_points: int, graph: bool = True):
+        self.handle = gvom_batch_create(max_maps, max_points, GVOM_BATCH_GRAPH if graph else 0)
+
+    def set_tuning(self, seg_len=16, march_block=256, march_blocks_per_sm=0):
+        gvom_batch_set_tuning(self.handle, gvom_tuning(seg_len, march_block, march_blocks_per_sm, 0))
+
+    def step(self, maps, vehicle_xyz, points, T_ws, outs=None, stream=None):
+        gvom_batch_step(self.handle, [m.handle for m in maps], vehicle_xyz, points, T_ws, outs, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gvom_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def gvom_microbench_red(buf, ops: int, seed: int = 1, stream=None) -> None:

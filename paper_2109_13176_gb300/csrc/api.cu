@@ -22,17 +22,6 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace gvom
 
-struct gvom_map {
-    gvom_config cfg;
-    long long origin[3];
-    MapState s;
-    gvom::RayScratch w;     // per-scan ray records and segment work list
-    float* height_scratch;  // nx * ny, used when the caller asks for no height
-    gvom_tuning tune;
-    long long scans;
-    long long points_in;
-    int device;
-};
 
 namespace gvom {
 
@@ -54,9 +43,7 @@ bool valid_config(const gvom_config* c) {
 
 }  // namespace gvom
 
-namespace {
-
-using gvom::valid_config;
+namespace gvom {
 
 Geom geom_of(const gvom_map* m) {
     Geom g;
@@ -112,14 +99,26 @@ bool valid_pose(const double T[12]) {
 }
 
 bool valid_tuning(const gvom_tuning* t) {
-    return t && t->seg_len >= 1 && t->seg_len <= 4096 && (t->march_block == 128 || t->march_block == 256 ||
-                                                          t->march_block == 512) &&
+    return t && t->seg_len >= 1 && t->seg_len <= 4096 && (t->march_block == 128 || t->march_block == 256) &&
            t->march_blocks_per_sm >= 0 && t->march_blocks_per_sm <= 32 && t->reserved == 0;
 }
 
 // Grows the ray records and the segment work list to hold a scan of n points
 // under the current segment length. Waits for the map's stream first when
 // buffers in use are replaced.
+}  // namespace gvom
+
+namespace {
+
+using gvom::cuda_status;
+using gvom::extract_params;
+using gvom::geom_of;
+using gvom::valid_config;
+using gvom::valid_origin;
+using gvom::valid_pose;
+using gvom::valid_tuning;
+using gvom::voxels;
+
 int ensure_capacity(gvom_map* m, long long n, cudaStream_t st) {
     const long long per_ray = gvom::max_segments_per_ray(geom_of(m), m->tune.seg_len);
     if (n <= m->w.cap_points && n * per_ray <= m->w.cap_items) return GVOM_OK;

@@ -1,0 +1,350 @@
+// Batched update of many independent maps (include/gvom.h, gvom_batch_*).
+//
+// One step folds one scan into each of B maps and, optionally, extracts
+// every map's 2D products, with five kernels for the whole batch instead of
+// five per map: the shifts of all maps (plus each map's quantised sensor),
+// the per-point pass over all maps' points, one persistent segment walk
+// over all maps' traversal segments (which balances maps of uneven size),
+// the column pass and the pixel pass. The per-step tables (each map's
+// pose, point pointer and count, shift, outputs, and the prefix counts the
+// kernels use to find a unit's map) are copied to the device from one of
+// two pinned buffers, and the kernels read every count from there, so the
+// five launches are captured once as a CUDA graph and replayed every step.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "gvom_internal.h"
+
+using gvom::BatchExtract;
+using gvom::BatchHeader;
+using gvom::BatchShift;
+using gvom::BatchTables;
+using gvom::ExtractParams;
+using gvom::Geom;
+using gvom::IngestArgs;
+
+namespace {
+
+size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Byte offsets of the table arrays inside one allocation.
+struct Layout {
+    size_t hdr, ing, sh, ex, shift_prefix, ray_prefix, ray_base, col_prefix, tile_prefix, sensors, bytes;
+};
+
+Layout layout_for(int max_maps) {
+    Layout L;
+    size_t o = 0;
+    L.hdr = o;
+    o = align16(o + sizeof(BatchHeader));
+    L.ing = o;
+    o = align16(o + sizeof(IngestArgs) * max_maps);
+    L.sh = o;
+    o = align16(o + sizeof(BatchShift) * max_maps);
+    L.ex = o;
+    o = align16(o + sizeof(BatchExtract) * max_maps);
+    L.shift_prefix = o;
+    o = align16(o + sizeof(long long) * (max_maps + 1));
+    L.ray_prefix = o;
+    o = align16(o + sizeof(long long) * (max_maps + 1));
+    L.ray_base = o;
+    o = align16(o + sizeof(long long) * max_maps);
+    L.col_prefix = o;
+    o = align16(o + sizeof(long long) * (max_maps + 1));
+    L.tile_prefix = o;
+    o = align16(o + sizeof(long long) * (max_maps + 1));
+    L.sensors = o;
+    o = align16(o + sizeof(int4) * max_maps);
+    L.bytes = o;
+    return L;
+}
+
+BatchTables tables_at(char* base, const Layout& L) {
+    BatchTables t;
+    t.hdr = reinterpret_cast<BatchHeader*>(base + L.hdr);
+    t.ing = reinterpret_cast<IngestArgs*>(base + L.ing);
+    t.sh = reinterpret_cast<BatchShift*>(base + L.sh);
+    t.ex = reinterpret_cast<BatchExtract*>(base + L.ex);
+    t.shift_prefix = reinterpret_cast<long long*>(base + L.shift_prefix);
+    t.ray_prefix = reinterpret_cast<long long*>(base + L.ray_prefix);
+    t.ray_base = reinterpret_cast<long long*>(base + L.ray_base);
+    t.col_prefix = reinterpret_cast<long long*>(base + L.col_prefix);
+    t.tile_prefix = reinterpret_cast<long long*>(base + L.tile_prefix);
+    t.sensors = reinterpret_cast<int4*>(base + L.sensors);
+    return t;
+}
+
+}  // namespace
+
+struct gvom_batch {
+    int max_maps;
+    long long max_points;
+    int flags;
+    Layout L;
+    char* d_tables;
+    char* h_tables[2];
+    cudaEvent_t copied[2];
+    int cur;
+    gvom::RayScratch w;
+    gvom_tuning tune;
+    // captured graph and what it was captured for
+    cudaGraphExec_t exec;
+    cudaStream_t cap_stream;
+    int g_B, g_extract, g_halo;
+    long long g_cap_items;
+    long long steps;
+    int64_t* new_o;  // 3 * max_maps: this step's origins
+};
+
+namespace {
+
+void free_scratch(gvom_batch* b) {
+    cudaFree(b->w.rays);
+    cudaFree(b->w.items);
+    b->w.rays = nullptr;
+    b->w.items = nullptr;
+    b->w.cap_points = 0;
+    b->w.cap_items = 0;
+}
+
+void drop_graph(gvom_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gvom_batch_create(int32_t max_maps, int64_t max_points, int32_t flags, gvom_batch** out) {
+    if (!out) return GVOM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_maps < 1 || max_maps > 4096 || max_points < 1 || max_points > GVOM_MAX_SCAN_POINTS ||
+        (flags & ~GVOM_BATCH_GRAPH) != 0)
+        return GVOM_ERR_INVALID_ARG;
+    gvom_batch* b = new (std::nothrow) gvom_batch();
+    if (!b) return GVOM_ERR_OUT_OF_MEMORY;
+    b->max_maps = max_maps;
+    b->max_points = max_points;
+    b->flags = flags;
+    b->L = layout_for(max_maps);
+    gvom_tuning_default(&b->tune);
+    cudaError_t e = cudaMalloc(&b->d_tables, b->L.bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tables[0], b->L.bytes);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_tables[1], b->L.bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&b->w.item_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&b->w.rays, sizeof(int4) * (size_t)max_points);
+    if (e == cudaSuccess) b->w.cap_points = max_points;
+    if (e == cudaSuccess) {
+        b->new_o = new (std::nothrow) int64_t[3 * (size_t)max_maps];
+        if (!b->new_o) e = cudaErrorMemoryAllocation;
+    }
+    if (e != cudaSuccess) {
+        gvom_batch_destroy(b);
+        cudaGetLastError();
+        return gvom::cuda_status(e);
+    }
+    memset(b->h_tables[0], 0, b->L.bytes);
+    memset(b->h_tables[1], 0, b->L.bytes);
+    *out = b;
+    return GVOM_OK;
+}
+
+void gvom_batch_destroy(gvom_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    free_scratch(b);
+    cudaFree(b->w.item_count);
+    cudaFree(b->d_tables);
+    cudaFreeHost(b->h_tables[0]);
+    cudaFreeHost(b->h_tables[1]);
+    if (b->copied[0]) cudaEventDestroy(b->copied[0]);
+    if (b->copied[1]) cudaEventDestroy(b->copied[1]);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete[] b->new_o;
+    delete b;
+}
+
+int gvom_batch_set_tuning(gvom_batch* b, const gvom_tuning* t) {
+    if (!b || !gvom::valid_tuning(t)) return GVOM_ERR_INVALID_ARG;
+    b->tune = *t;
+    drop_graph(b);
+    return GVOM_OK;
+}
+
+int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, const double* vehicle_xyz,
+                    const float* const* pts_dev, const int64_t* n, int32_t stride, const double* T_ws,
+                    const gvom_maps_out* outs, gvom_stream_t stream) {
+    if (!b || !maps || !vehicle_xyz || !pts_dev || !n || !T_ws || B < 1 || B > b->max_maps ||
+        (stride != 3 && stride != 4))
+        return GVOM_ERR_INVALID_ARG;
+    const cudaStream_t st = (cudaStream_t)stream;
+    // validate everything before any state changes
+    long long total = 0, items = 0;
+    int halo = 0;
+    for (int m = 0; m < B; ++m) {
+        const gvom_map* mp = maps[m];
+        if (!mp || n[m] < 0 || (n[m] > 0 && !pts_dev[m])) return GVOM_ERR_INVALID_ARG;
+        if ((((uintptr_t)pts_dev[m]) & (stride == 4 ? 15u : 3u)) != 0) return GVOM_ERR_INVALID_ARG;
+        if (!gvom::valid_pose(T_ws + 12 * m)) return GVOM_ERR_INVALID_ARG;
+        for (int k = 0; k < 3; ++k)
+            if (!isfinite(vehicle_xyz[3 * m + k])) return GVOM_ERR_INVALID_ARG;
+        for (int j = 0; j < m; ++j)
+            if (maps[j] == mp) return GVOM_ERR_INVALID_ARG;  // one update per map per step
+        total += n[m];
+        items += n[m] * gvom::max_segments_per_ray(gvom::geom_of(mp), b->tune.seg_len);
+        const int hm = gvom::tile_halo(gvom::extract_params(mp));
+        halo = hm > halo ? hm : halo;
+    }
+    if (total > b->max_points) return GVOM_ERR_INVALID_ARG;
+    int64_t* new_o = b->new_o;
+    for (int m = 0; m < B; ++m) {
+        const int rc = gvom_origin_for_pose(maps[m], vehicle_xyz + 3 * m, new_o + 3 * m);
+        if (rc != GVOM_OK) return rc;
+    }
+
+    // the segment work list for this step's points
+    if (items > b->w.cap_items) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return gvom::cuda_status(e);
+        cudaFree(b->w.items);
+        b->w.items = nullptr;
+        b->w.cap_items = 0;
+        long long cap = items + items / 4;
+        e = cudaMalloc(&b->w.items, sizeof(uint2) * (size_t)cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return GVOM_ERR_OUT_OF_MEMORY;
+        }
+        b->w.cap_items = cap;
+        drop_graph(b);
+    }
+
+    // fill this step's tables in the pinned buffer not in flight
+    const int cur = b->cur;
+    cudaError_t e = cudaEventSynchronize(b->copied[cur]);
+    if (e != cudaSuccess) return gvom::cuda_status(e);
+    BatchTables h = tables_at(b->h_tables[cur], b->L);
+    long long shift_total = 0, ray_blocks = 0, col_tasks = 0, tiles = 0, ray_base = 0;
+    for (int m = 0; m < B; ++m) {
+        gvom_map* mp = maps[m];
+        // window shift: the host copy of the origin moves now, in enqueue order
+        int d[3] = {0, 0, 0};
+        int whole = 0;
+        const int dims[3] = {mp->cfg.nx, mp->cfg.ny, mp->cfg.nz};
+        for (int k = 0; k < 3; ++k) {
+            const long long dk = new_o[3 * m + k] - mp->origin[k];
+            if (dk >= dims[k] || dk <= -dims[k]) whole = 1;
+            d[k] = (int)(whole ? 0 : dk);
+        }
+        if (whole) d[0] = d[1] = d[2] = 0;
+        for (int k = 0; k < 3; ++k) mp->origin[k] = new_o[3 * m + k];
+        const Geom g = gvom::geom_of(mp);
+        BatchShift& sh = h.sh[m];
+        sh.s = mp->s;
+        sh.g = g;
+        sh.d[0] = d[0];
+        sh.d[1] = d[1];
+        sh.d[2] = d[2];
+        sh.whole = whole;
+        h.shift_prefix[m] = shift_total;
+        shift_total += gvom::shift_units(g, d, whole);
+
+        IngestArgs& a = h.ing[m];
+        memset(&a, 0, sizeof(a));
+        a.pts = pts_dev[m];
+        a.n = n[m];
+        a.stride = stride;
+        a.seg_len = b->tune.seg_len;
+        for (int k = 0; k < 12; ++k) a.T[k] = T_ws[12 * m + k];
+        a.S = 256.0 * (1.0 / mp->cfg.res);
+        a.r2max = mp->cfg.max_range * mp->cfg.max_range;
+        for (int k = 0; k < 3; ++k) a.neg_o256[k] = -256.0 * (double)mp->origin[k];
+        a.g = g;
+        a.s = mp->s;
+        a.w = b->w;
+        h.ray_prefix[m] = ray_blocks;
+        ray_blocks += (n[m] + 255) / 256;
+        h.ray_base[m] = ray_base;
+        ray_base += n[m];
+        mp->scans += 1;
+        mp->points_in += n[m];
+
+        BatchExtract& ex = h.ex[m];
+        ex.s = mp->s;
+        ex.p = gvom::extract_params(mp);
+        const gvom_maps_out* o = outs ? outs + m : nullptr;
+        ex.height = (o && o->height_dev) ? o->height_dev : mp->height_scratch;
+        ex.density = o ? o->density_dev : nullptr;
+        ex.flags = o ? o->flags_dev : nullptr;
+        ex.slope = o ? o->slope_dev : nullptr;
+        ex.rough = o ? o->roughness_dev : nullptr;
+        h.col_prefix[m] = col_tasks;
+        col_tasks += ((long long)g.nx * g.ny + gvom::kColTask - 1) / gvom::kColTask;
+        h.tile_prefix[m] = tiles;
+        tiles += gvom::tiles_of(g);
+    }
+    h.shift_prefix[B] = shift_total;
+    h.ray_prefix[B] = ray_blocks;
+    h.col_prefix[B] = col_tasks;
+    h.tile_prefix[B] = tiles;
+    h.hdr->B = B;
+    h.hdr->shift_total = shift_total;
+    h.hdr->ray_blocks = ray_blocks;
+    h.hdr->col_tasks = outs ? col_tasks : 0;
+    h.hdr->tiles = outs ? tiles : 0;
+
+    e = cudaMemcpyAsync(b->d_tables, b->h_tables[cur], b->L.bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->copied[cur], st);
+    if (e != cudaSuccess) return gvom::cuda_status(e);
+    b->cur ^= 1;
+    b->steps += 1;
+
+    const BatchTables t = tables_at(b->d_tables, b->L);
+    IngestArgs shared;
+    memset(&shared, 0, sizeof(shared));
+    shared.w = b->w;
+    gvom::MarchShape shape;
+    shape.block = b->tune.march_block;
+    shape.blocks_per_sm = b->tune.march_blocks_per_sm;
+    const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
+    const int do_extract = outs != nullptr;
+
+    if (!(b->flags & GVOM_BATCH_GRAPH)) {
+        e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, st);
+        if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, halo, st);
+        return gvom::cuda_status(e);
+    }
+
+    if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items) {
+        drop_graph(b);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t le = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, b->cap_stream);
+            if (le == cudaSuccess && do_extract) le = gvom::launch_batch_extract(t, b->max_maps, halo, b->cap_stream);
+            e = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (e == cudaSuccess) e = le;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            cudaGetLastError();
+            return gvom::cuda_status(e);
+        }
+        b->g_extract = do_extract;
+        b->g_halo = halo;
+        b->g_cap_items = b->w.cap_items;
+    }
+    return gvom::cuda_status(cudaGraphLaunch(b->exec, st));
+}
+
+}  // extern "C"

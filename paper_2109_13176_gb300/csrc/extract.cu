@@ -57,13 +57,11 @@ __device__ __forceinline__ bool exceeds(float hi, float lo, float thresh) {
 }
 
 // Scalar column pass for any nz: one warp per column.
-__global__ void __launch_bounds__(kColBlock) k_columns_scalar(MapState s, ExtractParams p, float* __restrict__ height,
-                                                               float* __restrict__ density,
-                                                               uint8_t* __restrict__ flags) {
+__device__ __forceinline__ void column_scalar(const MapState& s, const ExtractParams& p, float* __restrict__ height,
+                                              float* __restrict__ density, uint8_t* __restrict__ flags,
+                                              long long col) {
     const Geom g = p.g;
-    const long long col = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (col >= (long long)g.nx * g.ny) return;
     const int cx = (int)(col / g.ny), cy = (int)(col % g.ny);
     int px = cx + g.rx;
     px -= (px >= g.nx) ? g.nx : 0;
@@ -122,106 +120,123 @@ __global__ void __launch_bounds__(kColBlock) k_columns_scalar(MapState s, Extrac
 // Vector column pass for nz % 4 == 0: LPC lanes per column, each lane
 // loading 16 bytes (4 voxels) per run and step, a grid-stride loop over
 // column groups.
+__global__ void __launch_bounds__(kColBlock) k_columns_scalar(MapState s, ExtractParams p, float* __restrict__ height,
+                                                               float* __restrict__ density,
+                                                               uint8_t* __restrict__ flags) {
+    const long long col = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
+    if (col >= (long long)p.g.nx * p.g.ny) return;
+    column_scalar(s, p, height, density, flags, col);
+}
+
+// One step of the vector column pass for one warp: lane group lane / LPC
+// takes column colb + lane / LPC (if below col_end); each lane loads 16
+// bytes (4 voxels) per run and step.
 template <int LPC>
-__global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams p, float* __restrict__ height,
-                                                        float* __restrict__ density, uint8_t* __restrict__ flags) {
+__device__ __forceinline__ void columns_step(const MapState& s, const ExtractParams& p, float* __restrict__ height,
+                                             float* __restrict__ density, uint8_t* __restrict__ flags,
+                                             long long colb, long long col_end) {
     const Geom g = p.g;
     const int lane = threadIdx.x & 31;
     const int sub = lane % LPC;                  // lane within the column group
     const unsigned gmask = (LPC == 32) ? 0xffffffffu : (((1u << LPC) - 1u) << (lane - sub));
-    const long long ncols = (long long)g.nx * g.ny;
-    const long long groups_per_warp = 32 / LPC;
-    const long long gtid = (long long)blockIdx.x * kColBlock + threadIdx.x;
-    const long long col0 = (gtid >> 5) * groups_per_warp + (lane / LPC);
-    const long long cstride = (((long long)gridDim.x * kColBlock) >> 5) * groups_per_warp;
     const int nv = g.nz >> 2;  // 16-byte vectors per run
     const float lof = p.obs_min_h, hif = p.obs_max_h;
-
-    for (long long colb = col0 - (lane / LPC); colb < ncols; colb += cstride) {
-        const long long col = colb + (lane / LPC);
-        const bool have = col < ncols;
-        int cx = 0, cy = 0;
-        size_t base = 0;
-        if (have) {
-            cx = (int)(col / g.ny);
-            cy = (int)(col % g.ny);
-            int px = cx + g.rx;
-            px -= (px >= g.nx) ? g.nx : 0;
-            int py = cy + g.ry;
-            py -= (py >= g.ny) ? g.ny : 0;
-            base = ((size_t)px * g.ny + py) * (size_t)g.nz;
-        }
-        const uint4* hc = reinterpret_cast<const uint4*>(s.hits + base);
-        const float4* mc = reinterpret_cast<const float4*>(s.minz + base);
-        float h = __int_as_float(0x7f800000);
-        bool any = false;
-        if (have) {
-            for (int v = sub; v < nv; v += LPC) {
-                const uint4 hv = __ldg(hc + v);
-                const float4 mv = __ldg(mc + v);
-                if (hv.x) { h = fminf(h, mv.x); any = true; }
-                if (hv.y) { h = fminf(h, mv.y); any = true; }
-                if (hv.z) { h = fminf(h, mv.z); any = true; }
-                if (hv.w) { h = fminf(h, mv.w); any = true; }
-            }
-        }
-#pragma unroll
-        for (int o = LPC / 2; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
-        const bool col_any = (__ballot_sync(0xffffffffu, any) & gmask) != 0u;
-
-        // Obstacle band: hits and passes summed over occupied voxels whose
-        // lowest return lies in [h + obs_min_h, h + obs_max_h] (FP64
-        // difference of the two floats, like the oracle).
-        unsigned long long H = 0, M = 0;
-        bool inband = false;
-        if (have && col_any) {
-            const uint4* pcv = reinterpret_cast<const uint4*>(s.passes + base);
-            for (int v = sub; v < nv; v += LPC) {
-                const uint4 hv = __ldg(hc + v);
-                const float4 mv = __ldg(mc + v);
-                const uint32_t hs[4] = {hv.x, hv.y, hv.z, hv.w};
-                const float ms[4] = {mv.x, mv.y, mv.z, mv.w};
-                bool need = false;
-                bool in[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    in[k] = hs[k] != 0u && in_band(ms[k], h, lof, hif);
-                    need |= in[k];
-                }
-                if (need) {
-                    const uint4 pv = __ldg(pcv + v);
-                    const uint32_t ps[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        if (in[k]) {
-                            H += hs[k];
-                            M += ps[k];
-                        }
-                    inband = true;
-                }
-            }
-        }
-        if (__ballot_sync(0xffffffffu, inband)) {  // warp-uniform: offsets stay inside a group
-#pragma unroll
-            for (int o = LPC / 2; o > 0; o >>= 1) {
-                H += __shfl_xor_sync(0xffffffffu, H, o);
-                M += __shfl_xor_sync(0xffffffffu, M, o);
-            }
-        }
-        if (have && sub == 0) {
-            const size_t o = (size_t)cx * g.ny + cy;
-            if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
-            uint8_t f = 0;
-            float dens = 0.0f;
-            if (H > 0) {
-                dens = density_of(H, H + M);
-                const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
-                f = hard ? 3 : 5;
-            }
-            if (density) density[o] = dens;
-            if (flags) flags[o] = f;
+    const long long col = colb + (lane / LPC);
+    const bool have = col < col_end;
+    int cx = 0, cy = 0;
+    size_t base = 0;
+    if (have) {
+        cx = (int)(col / g.ny);
+        cy = (int)(col % g.ny);
+        int px = cx + g.rx;
+        px -= (px >= g.nx) ? g.nx : 0;
+        int py = cy + g.ry;
+        py -= (py >= g.ny) ? g.ny : 0;
+        base = ((size_t)px * g.ny + py) * (size_t)g.nz;
+    }
+    const uint4* hc = reinterpret_cast<const uint4*>(s.hits + base);
+    const float4* mc = reinterpret_cast<const float4*>(s.minz + base);
+    float h = __int_as_float(0x7f800000);
+    bool any = false;
+    if (have) {
+        for (int v = sub; v < nv; v += LPC) {
+            const uint4 hv = __ldg(hc + v);
+            const float4 mv = __ldg(mc + v);
+            if (hv.x) { h = fminf(h, mv.x); any = true; }
+            if (hv.y) { h = fminf(h, mv.y); any = true; }
+            if (hv.z) { h = fminf(h, mv.z); any = true; }
+            if (hv.w) { h = fminf(h, mv.w); any = true; }
         }
     }
+#pragma unroll
+    for (int o = LPC / 2; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
+    const bool col_any = (__ballot_sync(0xffffffffu, any) & gmask) != 0u;
+
+    // Obstacle band: hits and passes summed over occupied voxels whose
+    // lowest return lies in [h + obs_min_h, h + obs_max_h] (FP64
+    // difference of the two floats, like the oracle).
+    unsigned long long H = 0, M = 0;
+    bool inband = false;
+    if (have && col_any) {
+        const uint4* pcv = reinterpret_cast<const uint4*>(s.passes + base);
+        for (int v = sub; v < nv; v += LPC) {
+            const uint4 hv = __ldg(hc + v);
+            const float4 mv = __ldg(mc + v);
+            const uint32_t hs[4] = {hv.x, hv.y, hv.z, hv.w};
+            const float ms[4] = {mv.x, mv.y, mv.z, mv.w};
+            bool need = false;
+            bool in[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                in[k] = hs[k] != 0u && in_band(ms[k], h, lof, hif);
+                need |= in[k];
+            }
+            if (need) {
+                const uint4 pv = __ldg(pcv + v);
+                const uint32_t ps[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (in[k]) {
+                        H += hs[k];
+                        M += ps[k];
+                    }
+                inband = true;
+            }
+        }
+    }
+    if (__ballot_sync(0xffffffffu, inband)) {  // warp-uniform: offsets stay inside a group
+#pragma unroll
+        for (int o = LPC / 2; o > 0; o >>= 1) {
+            H += __shfl_xor_sync(0xffffffffu, H, o);
+            M += __shfl_xor_sync(0xffffffffu, M, o);
+        }
+    }
+    if (have && sub == 0) {
+        const size_t o = (size_t)cx * g.ny + cy;
+        if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
+        uint8_t f = 0;
+        float dens = 0.0f;
+        if (H > 0) {
+            dens = density_of(H, H + M);
+            const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
+            f = hard ? 3 : 5;
+        }
+        if (density) density[o] = dens;
+        if (flags) flags[o] = f;
+    }
+}
+
+// Vector column pass for nz % 4 == 0: LPC lanes per column, a grid-stride
+// loop over column groups.
+template <int LPC>
+__global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams p, float* __restrict__ height,
+                                                        float* __restrict__ density, uint8_t* __restrict__ flags) {
+    const long long ncols = (long long)p.g.nx * p.g.ny;
+    const long long groups_per_warp = 32 / LPC;
+    const long long gw = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
+    const long long cstride = (((long long)gridDim.x * kColBlock) >> 5) * groups_per_warp;
+    for (long long colb = gw * groups_per_warp; colb < ncols; colb += cstride)
+        columns_step<LPC>(s, p, height, density, flags, colb, ncols);
 }
 
 constexpr int kTile = 16;
@@ -363,10 +378,9 @@ __device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* H
 // Block: warps 0-3 sweep the four cones (+x, -x, +y, -y) while warps 4-7
 // fit the planes of the defined pixels; then every thread combines the
 // cone values of one pixel.
-__global__ void __launch_bounds__(kPxBlock, 4)
-    k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
-                     float* __restrict__ rough, uint8_t* __restrict__ flags) {
-    extern __shared__ float smem[];
+__device__ __forceinline__ void tile_body(const ExtractParams& p, const float* __restrict__ height,
+                                          float* __restrict__ slope, float* __restrict__ rough,
+                                          uint8_t* __restrict__ flags, int tx0, int ty0, float* smem) {
     const int nx = p.g.nx, ny = p.g.ny;
     const int r = p.slope_n / 2;
     const int R = max(p.neg_max_px, r);
@@ -376,7 +390,6 @@ __global__ void __launch_bounds__(kPxBlock, 4)
     float* vals = Hs + W * W;                           // 4 * kTile^2 cone values
     float* Vbufs = vals + 4 * kTile * kTile;            // 4 * 2W
     unsigned char* Dbufs = reinterpret_cast<unsigned char*>(Vbufs + 8 * W);  // 4 * 2W
-    const int tx0 = blockIdx.y * kTile, ty0 = blockIdx.x * kTile;
     const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
 
@@ -412,9 +425,8 @@ __global__ void __launch_bounds__(kPxBlock, 4)
             if (rough) rough[o] = ro;
         }
     }
-    if (!flags) return;
     __syncthreads();
-    for (int t = threadIdx.x; t < kTile * kTile; t += blockDim.x) {
+    for (int t = threadIdx.x; flags && t < kTile * kTile; t += blockDim.x) {
         const int li = t / kTile, lj = t % kTile;
         const int cx = tx0 + li, cy = ty0 + lj;
         if (cx >= nx || cy >= ny) continue;
@@ -431,13 +443,80 @@ __global__ void __launch_bounds__(kPxBlock, 4)
         }
         if (nf >= 2 && exceeds(hi, lo, p.neg_thresh)) flags[(size_t)cx * ny + cy] |= 8u;
     }
+    __syncthreads();  // the caller may reuse the shared arrays for its next tile
 }
 
-size_t slope_negative_smem(const ExtractParams& p) {
-    const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
+__global__ void __launch_bounds__(kPxBlock, 4)
+    k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
+                     float* __restrict__ rough, uint8_t* __restrict__ flags) {
+    extern __shared__ float smem[];
+    tile_body(p, height, slope, rough, flags, blockIdx.y * kTile, blockIdx.x * kTile, smem);
+}
+
+// ---- batched maps ----------------------------------------------------------
+
+__device__ __forceinline__ int find_map_x(const long long* __restrict__ prefix, int B, long long u) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Column pass of all maps: persistent warps over 64-column tasks.
+__global__ void __launch_bounds__(kColBlock) k_columns_batch(BatchTables t) {
+    const int B = t.hdr->B;
+    const long long total = t.hdr->col_tasks;
+    const long long nwarps = ((long long)gridDim.x * kColBlock) >> 5;
+    for (long long u = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5; u < total; u += nwarps) {
+        const int m = find_map_x(t.col_prefix, B, u);
+        const BatchExtract& ex = t.ex[m];
+        const long long ncols = (long long)ex.p.g.nx * ex.p.g.ny;
+        const long long c0 = (u - t.col_prefix[m]) * kColTask;
+        const long long c1 = c0 + kColTask < ncols ? c0 + kColTask : ncols;
+        const int nz = ex.p.g.nz;
+        if ((nz & 3) == 0) {
+            const int nv = nz >> 2;
+            if (nv <= 8) {
+                for (long long c = c0; c < c1; c += 4) columns_step<8>(ex.s, ex.p, ex.height, ex.density, ex.flags, c, c1);
+            } else if (nv <= 16) {
+                for (long long c = c0; c < c1; c += 2)
+                    columns_step<16>(ex.s, ex.p, ex.height, ex.density, ex.flags, c, c1);
+            } else {
+                for (long long c = c0; c < c1; c += 1)
+                    columns_step<32>(ex.s, ex.p, ex.height, ex.density, ex.flags, c, c1);
+            }
+        } else {
+            for (long long c = c0; c < c1; ++c) column_scalar(ex.s, ex.p, ex.height, ex.density, ex.flags, c);
+        }
+    }
+}
+
+// Plane-fit / cone pass of all maps: a persistent grid over pixel tiles.
+__global__ void __launch_bounds__(kPxBlock, 4) k_slope_negative_batch(BatchTables t) {
+    extern __shared__ float smem[];
+    const int B = t.hdr->B;
+    const long long total = t.hdr->tiles;
+    for (long long u = blockIdx.x; u < total; u += gridDim.x) {
+        const int m = find_map_x(t.tile_prefix, B, u);
+        const BatchExtract& ex = t.ex[m];
+        const long long lt = u - t.tile_prefix[m];
+        const int tiles_y = (ex.p.g.ny + kTile - 1) / kTile;
+        tile_body(ex.p, ex.height, ex.slope, ex.rough, ex.flags, (int)(lt / tiles_y) * kTile,
+                  (int)(lt % tiles_y) * kTile, smem);
+    }
+}
+
+size_t slope_negative_smem_halo(int R) {
     const int W = kTile + 2 * R;
     return sizeof(float) * ((size_t)W * W + 4 * kTile * kTile + 8 * (size_t)W) + 8 * (size_t)W;
 }
+
+size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_halo(tile_halo(p)); }
 
 __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits, uint32_t* __restrict__ passes,
                                 float* __restrict__ minz) {
@@ -468,6 +547,27 @@ int sm_count() {
 }
 
 }  // namespace
+
+int tile_halo(const ExtractParams& p) { return p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2; }
+
+long long tiles_of(const Geom& g) { return (long long)((g.nx + kTile - 1) / kTile) * ((g.ny + kTile - 1) / kTile); }
+
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st) {
+    (void)max_maps;
+    const int sms = sm_count();
+    count_launch();
+    k_columns_batch<<<(unsigned)(sms * 8), kColBlock, 0, st>>>(t);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = slope_negative_smem_halo(max_halo);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_slope_negative_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    count_launch();
+    k_slope_negative_batch<<<(unsigned)(sms * 4), kPxBlock, smem, st>>>(t);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density, uint8_t* flags,
                            cudaStream_t st) {

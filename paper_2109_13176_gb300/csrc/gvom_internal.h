@@ -70,6 +70,60 @@ struct ExtractParams {
     float neg_thresh;
 };
 
+// ---- Batched update of many maps (tables filled by the host each step) ----
+
+// Window shift of one map in a batch step.
+struct BatchShift {
+    MapState s;
+    Geom g;          // the new window
+    int d[3];        // new - old origin (|d_k| < n_k unless whole)
+    int whole;       // 1: clear the whole map
+};
+
+// Extraction of one map in a batch step.
+struct BatchExtract {
+    MapState s;
+    ExtractParams p;
+    float* height;   // never null (the map's scratch when the caller asked for none)
+    float* density;
+    uint8_t* flags;
+    float* slope;
+    float* rough;
+};
+
+// Step totals, read by the kernels from device memory so that a captured
+// graph replays with new counts.
+struct BatchHeader {
+    int B;
+    int pad;
+    long long shift_total;   // warp units of the shift kernel
+    long long ray_blocks;    // 256-point blocks of the per-point pass
+    long long col_tasks;     // 64-column warp tasks of the column pass
+    long long tiles;         // pixel tiles of the plane-fit / cone pass
+};
+
+// Device pointers into one allocation of a batch's tables.
+struct BatchTables {
+    BatchHeader* hdr;
+    IngestArgs* ing;          // [max_maps]
+    BatchShift* sh;           // [max_maps]
+    BatchExtract* ex;         // [max_maps]
+    long long* shift_prefix;  // [max_maps + 1]
+    long long* ray_prefix;    // [max_maps + 1], in 256-point blocks
+    long long* ray_base;      // [max_maps], first ray record of each map
+    long long* col_prefix;    // [max_maps + 1], in tasks
+    long long* tile_prefix;   // [max_maps + 1]
+    int4* sensors;            // [max_maps], written on the device
+};
+
+constexpr int kColTask = 64;       // columns per warp task of the batched column pass
+long long shift_units(const Geom& g, const int d[3], int whole);
+long long tiles_of(const Geom& g);
+int tile_halo(const ExtractParams& p);
+cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
+                                const MarchShape& shape, cudaStream_t st);
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st);
+
 // Whether a configuration is within the documented limits (include/gvom.h).
 bool valid_config(const gvom_config* c);
 
@@ -94,4 +148,28 @@ __host__ __device__ inline long long floor_mod(long long a, long long n) {
     return r < 0 ? r + n : r;
 }
 
+}  // namespace gvom
+
+// One map (include/gvom.h): configuration, window origin (host copy, updated
+// in enqueue order), device state and per-scan scratch.
+struct gvom_map {
+    gvom_config cfg;
+    long long origin[3];
+    gvom::MapState s;
+    gvom::RayScratch w;     // per-scan ray records and segment work list
+    float* height_scratch;  // nx * ny, used when the caller asks for no height
+    gvom_tuning tune;
+    long long scans;
+    long long points_in;
+    int device;
+};
+
+namespace gvom {
+Geom geom_of(const gvom_map* m);
+long long voxels(const gvom_map* m);
+int cuda_status(cudaError_t e);
+bool valid_origin(const int64_t o[3]);
+ExtractParams extract_params(const gvom_map* m);
+bool valid_pose(const double T[12]);
+bool valid_tuning(const gvom_tuning* t);
 }  // namespace gvom

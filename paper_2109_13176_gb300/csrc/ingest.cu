@@ -144,16 +144,17 @@ __device__ __forceinline__ bool ray_frame(const Geom& g, const int a[3], const i
 }
 
 // Phase 1: points -> hits, lowest returns, ray records and segment list.
-__global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
-    const long long i = (long long)blockIdx.x * kRaysBlock + threadIdx.x;
+// Called by every thread of a block, for points i = first + threadIdx.x of
+// one map (map_id) whose ray records start at ray_base in the scratch.
+__device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, const int qo[3], bool sensor_ok,
+                                          long long ray_base, unsigned int map_id) {
+    const long long i = first + threadIdx.x;
     const Geom g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     bool valid = false;
     int q[3] = {0, 0, 0};
     float wz = 0.0f;
-    int qo[3];
-    const bool sensor_ok = block_sensor(a, qo);
 
     if (i < a.n) {
         const float* p = a.pts + i * a.stride;
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
         RayFrame f;
         if (ray_frame(g, qo, q, f)) nseg = (f.khi - f.klo) / a.seg_len + 1;
     }
-    if (i < a.n) a.w.rays[i] = make_int4(q[0], q[1], q[2], nseg);
+    if (i < a.n) a.w.rays[ray_base + i] = make_int4(q[0], q[1], q[2], (int)((map_id << 16) | (unsigned)nseg));
 
     // Reserve this block's slots in the work list with one atomic, then lay
     // each warp's segments out segment-major (all first segments of the
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
         const unsigned int m = __ballot_sync(0xffffffffu, nseg > j);
         if (nseg > j) {
             const unsigned long long slot = off + __popc(m & lt);
-            if (slot < (unsigned long long)a.w.cap_items) a.w.items[slot] = make_uint2((unsigned int)i, (unsigned int)j);
+            if (slot < (unsigned long long)a.w.cap_items)
+                a.w.items[slot] = make_uint2((unsigned int)(ray_base + i), (unsigned int)j);
         }
         off += __popc(m);
     }
@@ -245,6 +247,13 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
         for (int w = 0; w < kRaysBlock / 32; ++w) s += red[threadIdx.x][w];
         if (s) atomicAdd(a.s.counters + kRaysValid + threadIdx.x, s);
     }
+    __syncthreads();  // the shared arrays are reused by the caller's next block
+}
+
+__global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
+    int qo[3];
+    const bool sensor_ok = block_sensor(a, qo);
+    rays_body(a, (long long)blockIdx.x * kRaysBlock, qo, sensor_ok, 0, 0u);
 }
 
 // Phase 2: walk the segments.
@@ -407,27 +416,44 @@ __device__ __forceinline__ uint32_t walk_index(const Walk& w) {
     return (uint32_t)pM * w.kM + (uint32_t)pA * w.kA + (uint32_t)pB * w.kB;
 }
 
-__global__ void k_march(const IngestArgs a) {
+// kBatch = false: one map, whose arguments are a1. kBatch = true: many maps;
+// a1 carries only the shared scratch (work list and ray records), each ray
+// record names its map, and descs / sensors hold each map's arguments and
+// quantised sensor position. Pass increments of lanes of different maps
+// never merge: lanes match on the full address.
+template <bool kBatch>
+__global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     const int lane = threadIdx.x & 31;
-    const unsigned long long total_items = *a.w.item_count;
+    const unsigned long long total_items = *a1.w.item_count;
     const long long n_items =
-        (long long)(total_items < (unsigned long long)a.w.cap_items ? total_items : a.w.cap_items);
+        (long long)(total_items < (unsigned long long)a1.w.cap_items ? total_items : a1.w.cap_items);
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 
-    int qo[3];
-    block_sensor(a, qo);  // the work list only holds rays of a quantisable sensor
+    int qo1[3] = {0, 0, 0};
+    if (!kBatch) block_sensor(a1, qo1);  // the work list only holds rays of a quantisable sensor
 
     unsigned long long visits = 0;
     for (long long base = gw * 32; base < n_items; base += nwarps * 32) {
         const long long idx = base + lane;
         Walk w;
         bool live = false;
+        unsigned int map = 0;
+        uint32_t* passes = a1.s.passes;
+        unsigned long long item_visits = 0;
         if (idx < n_items) {
-            const uint2 it = a.w.items[idx];
-            const int4 r = a.w.rays[it.x];
+            const uint2 it = a1.w.items[idx];
+            const int4 r = a1.w.rays[it.x];
             const int b[3] = {r.x, r.y, r.z};
-            live = walk_init(a, qo, b, (int)it.y, w);
+            if (kBatch) {
+                map = (unsigned int)r.w >> 16;
+                const int4 sq = sensors[map];
+                const int qo[3] = {sq.x, sq.y, sq.z};
+                passes = descs[map].s.passes;
+                live = walk_init(descs[map], qo, b, (int)it.y, w);
+            } else {
+                live = walk_init(a1, qo1, b, (int)it.y, w);
+            }
         }
         // Visit the current voxel, then take the next crossing group,
         // unless it moves the major axis past this segment. The ray's last
@@ -443,10 +469,14 @@ __global__ void k_march(const IngestArgs a) {
                     if (inside) key = walk_index(w);
                 }
             }
-            const unsigned int peers = __match_any_sync(0xffffffffu, key);
+            unsigned int peers;
+            if (kBatch)
+                peers = __match_any_sync(0xffffffffu, inside ? (unsigned long long)(passes + key) : 0ull);
+            else
+                peers = __match_any_sync(0xffffffffu, key);
             if (inside) {
-                if (lane == __ffs(peers) - 1) atomicAdd(a.s.passes + key, (uint32_t)__popc(peers));
-                visits += 1;
+                if (lane == __ffs(peers) - 1) atomicAdd(passes + key, (uint32_t)__popc(peers));
+                item_visits += 1;
             }
             if (!live) continue;
             const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
@@ -470,12 +500,29 @@ __global__ void k_march(const IngestArgs a) {
             // so it passes the window exactly at its exit voxel)
             if (w.cA == w.exitA || w.cB == w.exitB) live = false;
         }
+        if (kBatch) {
+            // counters per map: one atomic per warp when all lanes share a map
+            int all_same = 0;
+            __match_all_sync(0xffffffffu, map, &all_same);
+            if (all_same) {
+                unsigned long long v = item_visits;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0 && v) atomicAdd(descs[map].s.counters + kPassVisits, v);
+            } else if (item_visits) {
+                atomicAdd(descs[map].s.counters + kPassVisits, item_visits);
+            }
+        } else {
+            visits += item_visits;
+        }
     }
 
-    // Counter: one atomic per warp of the persistent grid.
+    if (!kBatch) {
+        // Counter: one atomic per warp of the persistent grid.
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
-    if (lane == 0 && visits) atomicAdd(a.s.counters + kPassVisits, visits);
+        for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
+        if (lane == 0 && visits) atomicAdd(a1.s.counters + kPassVisits, visits);
+    }
 }
 
 // Fill the state with the empty voxel: no hits, no passes, min height +inf.
@@ -545,6 +592,101 @@ __global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
     }
 }
 
+// ---- batched maps ----------------------------------------------------------
+
+// The map m whose range [prefix[m], prefix[m+1]) holds unit u (0 <= u <
+// prefix[B]): the largest m with prefix[m] <= u.
+__device__ __forceinline__ int find_map(const long long* __restrict__ prefix, int B, long long u) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Window shifts of all maps of a batch step, one warp per unit (a whole
+// entering column, 32 z-slab columns, or 1024 voxels of a map cleared
+// whole), plus each map's quantised sensor position.
+__global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
+    const int B = t.hdr->B;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < B) {
+        const IngestArgs& a = t.ing[tid];
+        int q[3];
+        bool ok = true;
+        for (int k = 0; k < 3; ++k) ok &= quantise(a.T[4 * k + 3], a.S, a.neg_o256[k], &q[k]);
+        t.sensors[tid] = make_int4(q[0], q[1], q[2], ok ? 1 : 0);
+    }
+    const int lane = threadIdx.x & 31;
+    const long long total = t.hdr->shift_total;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = tid >> 5; u < total; u += nwarps) {
+        const int m = find_map(t.shift_prefix, B, u);
+        const long long lu = u - t.shift_prefix[m];
+        const BatchShift& sh = t.sh[m];
+        const Geom g = sh.g;
+        if (sh.whole) {
+            const long long V = (long long)g.nx * g.ny * g.nz;
+            const long long v0 = lu * 1024;
+            for (long long v = v0 + lane; v < v0 + 1024 && v < V; v += 32) clear_voxel(sh.s, (uint32_t)v);
+            continue;
+        }
+        const int dx = sh.d[0], dy = sh.d[1], dz = sh.d[2];
+        const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
+        const long long n_xslab = (long long)adx * g.ny;
+        const long long n_cols = n_xslab + (long long)(g.nx - adx) * ady;
+        if (lu < n_cols) {
+            int cx, cy;
+            if (lu < n_xslab) {
+                const int k = (int)(lu / g.ny);
+                cx = dx > 0 ? g.nx - dx + k : k;
+                cy = (int)(lu % g.ny);
+            } else {
+                const long long w = lu - n_xslab;
+                const int k = (int)(w / ady), l = (int)(w % ady);
+                cx = (dx > 0 ? 0 : adx) + k;
+                cy = dy > 0 ? g.ny - dy + l : l;
+            }
+            const uint32_t base = column_base(g, cx, cy);
+            for (int cz = lane; cz < g.nz; cz += 32) clear_voxel(sh.s, base + (uint32_t)cz);
+        } else {
+            // 32 z-slab columns per unit, one per lane
+            const int wy = g.ny - ady;
+            const long long w = (lu - n_cols) * 32 + lane;
+            if (w >= (long long)(g.nx - adx) * wy) continue;
+            const int cx = (dx > 0 ? 0 : adx) + (int)(w / wy);
+            const int cy = (dy > 0 ? 0 : ady) + (int)(w % wy);
+            const uint32_t base = column_base(g, cx, cy);
+            const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
+            for (int cz = z0; cz < z1; ++cz) {
+                int pz = cz + g.rz;
+                pz -= (pz >= g.nz) ? g.nz : 0;
+                clear_voxel(sh.s, base + (uint32_t)pz);
+            }
+        }
+    }
+}
+
+// Per-point pass of all maps: a persistent grid over the maps' 256-point
+// blocks; every block belongs to one map.
+__global__ void __launch_bounds__(kRaysBlock) k_rays_batch(BatchTables t) {
+    __shared__ int s_m;
+    const int B = t.hdr->B;
+    const long long total = t.hdr->ray_blocks;
+    for (long long vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        if (threadIdx.x == 0) s_m = find_map(t.ray_prefix, B, vb);
+        __syncthreads();
+        const int m = s_m;
+        const int4 sq = t.sensors[m];
+        const int qo[3] = {sq.x, sq.y, sq.z};
+        rays_body(t.ing[m], (vb - t.ray_prefix[m]) * kRaysBlock, qo, sq.w != 0, t.ray_base[m], (unsigned int)m);
+    }
+}
+
 // Blocks of the persistent segment walk: every SM filled to its occupancy.
 int march_grid(const MarchShape& shape) {
     int dev = 0, sms = 0, nb = 0;
@@ -553,13 +695,44 @@ int march_grid(const MarchShape& shape) {
     if (sms <= 0) sms = 1;
     int per_sm = shape.blocks_per_sm;
     if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march, shape.block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<false>, shape.block, 0);
         per_sm = nb > 0 ? nb : 1;
     }
     return sms * per_sm;
 }
 
 }  // namespace
+
+long long shift_units(const Geom& g, const int d[3], int whole) {
+    if (whole) return ((long long)g.nx * g.ny * g.nz + 1023) / 1024;
+    const long long adx = d[0] < 0 ? -d[0] : d[0], ady = d[1] < 0 ? -d[1] : d[1];
+    long long u = adx * g.ny + (g.nx - adx) * ady;
+    if (d[2] != 0) u += ((g.nx - adx) * (g.ny - ady) + 31) / 32;
+    return u;
+}
+
+cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
+                                const MarchShape& shape, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    cudaError_t e = cudaMemsetAsync(shared.w.item_count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    long long sblocks = (long long)sms * 8;
+    if (sblocks * 256 < max_maps) sblocks = (max_maps + 255) / 256;
+    count_launch();
+    k_shift_batch<<<(unsigned)sblocks, 256, 0, st>>>(t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    long long rblocks = (long long)sms * 8;
+    if (rblocks > max_ray_blocks) rblocks = max_ray_blocks > 0 ? max_ray_blocks : 1;
+    count_launch();
+    k_rays_batch<<<(unsigned)rblocks, kRaysBlock, 0, st>>>(t);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launch();
+    k_march<true><<<march_grid(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
+    return cudaGetLastError();
+}
 
 long long max_segments_per_ray(const Geom& g, int seg_len) {
     const int n = g.nx > g.ny ? (g.nx > g.nz ? g.nx : g.nz) : (g.ny > g.nz ? g.ny : g.nz);
@@ -611,7 +784,7 @@ cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStre
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_march<<<march_grid(shape), shape.block, 0, st>>>(a);
+    k_march<false><<<march_grid(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
     return cudaGetLastError();
 }
 
