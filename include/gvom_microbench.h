@@ -25,7 +25,8 @@ GVOM_API int gvom_microbench_red(uint32_t* buf_dev, int64_t words, int64_t ops, 
                                  gvom_stream_t stream);
 
 /* Number of kernels this library has launched since it was loaded (all
- * maps, all entry points). Host-only; instrumentation for benchmarks. */
+ * maps, all entry points; a replay of a captured batch step counts the
+ * kernels the graph holds). Host-only; instrumentation for benchmarks. */
 GVOM_API int64_t gvom_kernel_launches(void);
 
 #ifdef __cplusplus

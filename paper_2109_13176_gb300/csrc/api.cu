@@ -19,7 +19,7 @@ using gvom::MapState;
 
 namespace gvom {
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace gvom
 
 

@@ -16,6 +16,7 @@
 #include <new>
 
 #include "gvom_internal.h"
+#include "../../include/gvom_microbench.h"
 
 using gvom::BatchExtract;
 using gvom::BatchHeader;
@@ -94,6 +95,7 @@ struct gvom_batch {
     cudaStream_t cap_stream;
     int g_B, g_extract, g_halo;
     long long g_cap_items;
+    long long g_kernels;  // kernels in the captured graph, counted per replay
     long long steps;
     int64_t* new_o;  // 3 * max_maps: this step's origins
 };
@@ -326,6 +328,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
+        const long long before = gvom_kernel_launches();
         e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t le = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, b->cap_stream);
@@ -343,7 +346,10 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         b->g_extract = do_extract;
         b->g_halo = halo;
         b->g_cap_items = b->w.cap_items;
+        b->g_kernels = gvom_kernel_launches() - before;
+        gvom::count_launch(-b->g_kernels);  // captured, not launched
     }
+    gvom::count_launch(b->g_kernels);
     return gvom::cuda_status(cudaGraphLaunch(b->exec, st));
 }
 

@@ -127,8 +127,9 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
 // Whether a configuration is within the documented limits (include/gvom.h).
 bool valid_config(const gvom_config* c);
 
-// Counts kernel launches (gvom_kernel_launches).
-void count_launch();
+// Counts kernel launches (gvom_kernel_launches); graph replays add the
+// number of kernels the graph holds.
+void count_launch(long long n = 1);
 
 // Launchers (return the CUDA error of the launch).
 cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st);

@@ -1,0 +1,125 @@
+"""Autotuner for the traversal launch shape (gvom_tuning).
+
+The segment walk's speed depends on the segment length (shorter segments
+balance warps better but cost more set-up) and on the block shape of its
+persistent grid; the best pair depends on the map, the sensor and the GPU.
+The tuner times each candidate on the caller's own workload, keeps the
+fastest, and remembers it in a JSON table (GVOM_TUNE_CACHE, default
+~/.cache/gvom/tuning.json) under a key naming the device and the workload,
+so later runs skip the search. Results never depend on the tuning, only time.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+import time
+
+CANDIDATES = [(L, blk, 0) for L in (6, 8, 12, 16, 24) for blk in (128, 256)]
+
+
+def cache_path() -> str:
+    return os.environ.get("GVOM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "gvom", "tuning.json"))
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(table: dict) -> None:
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(table, fh, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass
+
+
+def workload_key(kind: str, dims, res: float, points: int) -> str:
+    import torch
+    dev = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    bucket = 1 << max(0, int(points).bit_length() - 1)  # power-of-two bucket of the point count
+    return f"{dev}|{kind}|{'x'.join(str(int(d)) for d in dims)}@{res:g}|~{bucket}"
+
+
+def search(run, candidates=CANDIDATES, repeats: int = 3):
+    """run(candidate) -> seconds of one timed repetition; returns (best, table)."""
+    times = {}
+    for c in candidates:
+        run(c)  # warm-up (first launch, scratch growth)
+        times[c] = statistics.median(run(c) for _ in range(repeats))
+    best = min(times, key=times.get)
+    return best, {f"{c[0]}/{c[1]}/{c[2]}": round(t * 1e6, 2) for c, t in times.items()}
+
+
+def tuned(key: str, run, candidates=CANDIDATES, repeats: int = 3, refresh: bool = False):
+    """The cached best candidate for key, or a fresh search (then cached)."""
+    table = _load()
+    if not refresh and key in table:
+        c = table[key]["best"]
+        return tuple(c), table[key]
+    t0 = time.perf_counter()
+    best, times = search(run, candidates, repeats)
+    entry = {"best": list(best), "us": times, "search_s": round(time.perf_counter() - t0, 2)}
+    table[key] = entry
+    _store(table)
+    return best, entry
+
+
+def tune_map(vmap, scans_dev, poses, vehicles, flush=None, refresh: bool = False, repeats: int = 3):
+    """Tunes one VoxelMap's ingest on a few of its own scans (CUDA tensors)."""
+    import torch
+    stream = torch.cuda.current_stream()
+
+    def run(c):
+        vmap.set_tuning(*c)
+        tot = 0.0
+        for pts, T, v in zip(scans_dev, poses, vehicles):
+            vmap.shift(vmap.origin_for_pose(v))
+            if flush is not None:
+                flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            vmap.ingest(pts, T)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+        return tot
+
+    key = workload_key("map", vmap.shape, vmap.cfg.res, int(statistics.median(int(p.shape[0]) for p in scans_dev)))
+    best, entry = tuned(key, run, repeats=repeats, refresh=refresh)
+    vmap.set_tuning(*best)
+    return best, entry
+
+
+def tune_batch(batch, maps, step_inputs, flush=None, refresh: bool = False, repeats: int = 2):
+    """Tunes a MapBatch on its own steps: step_inputs = [(vehicles, scans, poses), ...]."""
+    import torch
+    stream = torch.cuda.current_stream()
+
+    def run(c):
+        batch.set_tuning(*c)
+        tot = 0.0
+        for vs, scans, Ts in step_inputs:
+            if flush is not None:
+                flush()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.step(maps, vs, scans, Ts)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) * 1e-3
+        return tot
+
+    pts = sum(int(p.shape[0]) for p in step_inputs[0][1])
+    key = workload_key(f"batch{len(maps)}", maps[0].shape, maps[0].cfg.res, pts)
+    best, entry = tuned(key, run, repeats=repeats, refresh=refresh)
+    batch.set_tuning(*best)
+    return best, entry

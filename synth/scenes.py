@@ -19,8 +19,10 @@ Recipes (seed = SEED_BASE + config number, sub-seeds by map/robot index):
    20 % of the rays entering a cluster return inside it at a uniform depth
    and the rest pass through.
 4. Batched: 64 maps of the sequence kind, each with its own terrain and
-   trajectory; each map's scan per step is a seeded random subset (scan order
-   kept) of a 128 x 2048 scan, of size floor(exp U(ln 8192, ln 262144)).
+   trajectory (terrain modelled 70 m around the route; beyond it the ground
+   continues at the edge height); each map's scan per step is a seeded
+   random subset (scan order kept) of a 128 x 2048 scan, of size
+   floor(exp U(ln 8192, ln 262144)).
 5. Served: 32 robots with mixed sensors (16/64/128 beams) and maps, arrivals
    with exponential inter-arrival times (mean 100 ms), over a stream of
    given length; each robot draws its scans from a small pool of consecutive
@@ -409,9 +411,9 @@ def _trajectory_pose(scene: Scene, speed: float, t: float, x_start: float = 0.0,
     return np.array([X, Y, z]), yaw, pitch
 
 
-def make_sequence_scene(cfg: SequenceConfig, rng, yaw0: float = 0.0) -> Scene:
+def make_sequence_scene(cfg: SequenceConfig, rng, yaw0: float = 0.0, extent: float = 110.0) -> Scene:
     route = cfg.speed * cfg.n_scans / cfg.rate_hz
-    ext = 110.0
+    ext = extent
     sc = random_scene(rng, (-25.0, route + 25.0), (-25.0, 25.0), rough=cfg.rough,
                       veg_clusters=cfg.veg_clusters, raster=0.1 if cfg.rough > 0 else 0.2,
                       path=(lambda x: float(_path_y(x))) if yaw0 == 0.0 else None)
@@ -419,46 +421,81 @@ def make_sequence_scene(cfg: SequenceConfig, rng, yaw0: float = 0.0) -> Scene:
     return sc
 
 
-def sequence_scans(k: int, n_scans: int | None = None, seed: int | None = None,
-                   stride: int = 1):
-    """Scans 0, stride, 2*stride, ... of sequence configuration k (2 or 3)."""
+def _sequence_chunk(args):
+    k, seed, steps = args
     cfg = sequence_config(k)
-    seed = SEED_BASE + k if seed is None else seed
     rng = np.random.default_rng(seed)
     sc = make_sequence_scene(cfg, rng)
-    n = cfg.n_scans if n_scans is None else n_scans
     out = []
-    for i in range(n):
-        step = i * stride
+    for step in steps:
         t = step / cfg.rate_hz
         veh, yaw, pitch = _trajectory_pose(sc, cfg.speed, t)
         T = pose_matrix(veh, yaw, pitch)
         srng = np.random.default_rng([seed, 1, step])
         out.append(scan_from_pose(sc, cfg.lidar, T, veh, srng, t=t))
-    return cfg, out
+    return out
+
+
+def sequence_scans(k: int, n_scans: int | None = None, seed: int | None = None,
+                   stride: int = 1, workers: int = 0):
+    """Scans 0, stride, 2*stride, ... of sequence configuration k (2 or 3).
+
+    workers > 1 casts the scans in a spawn-started process pool (each worker
+    rebuilds the same seeded scene; the scans are identical)."""
+    cfg = sequence_config(k)
+    seed = SEED_BASE + k if seed is None else seed
+    n = cfg.n_scans if n_scans is None else n_scans
+    steps = [i * stride for i in range(n)]
+    if workers and workers > 1 and n > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        w = min(workers, n)
+        chunks = [steps[i::w] for i in range(w)]
+        with ProcessPoolExecutor(max_workers=w, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_sequence_chunk, [(k, seed, c) for c in chunks]))
+        by_step = {}
+        for c, part in zip(chunks, parts):
+            for st, scan in zip(c, part):
+                by_step[st] = scan
+        return cfg, [by_step[st] for st in steps]
+    return cfg, _sequence_chunk((k, seed, steps))
+
+
+def _batched_map(args):
+    """Scene, trajectory and n_steps scans of one map of the batched workload."""
+    seed, m, n_steps, lo, hi = args
+    cfg = SequenceConfig(MapSpec(256, 256, 64, 0.2), LidarSpec(128, 2048, 22.5), n_steps, 4.5)
+    r = np.random.default_rng([seed, 0, m])
+    yaw0 = float(r.uniform(0, 2 * np.pi))
+    sc = make_sequence_scene(cfg, r, yaw0=yaw0, extent=70.0)
+    out = []
+    for s in range(n_steps):
+        rs = np.random.default_rng([seed, 1, m, s])
+        size = int(math.floor(math.exp(rs.uniform(math.log(lo), math.log(hi)))))
+        subset = np.sort(rs.choice(cfg.lidar.n, size=size, replace=False))
+        t = s / cfg.rate_hz
+        veh, yaw, pitch = _trajectory_pose(sc, cfg.speed, t, yaw0=yaw0)
+        T = pose_matrix(veh, yaw, pitch)
+        out.append(scan_from_pose(sc, cfg.lidar, T, veh, rs, subset=subset, t=t))
+    return out
 
 
 def batched_scans(n_maps: int = 64, n_steps: int = 1, seed: int = SEED_BASE + 4,
-                  lo: int = 8192, hi: int = 262144):
-    """Per step, a list of n_maps scans of log-uniform size (configuration 4)."""
+                  lo: int = 8192, hi: int = 262144, workers: int = 0):
+    """Per step, a list of n_maps scans of log-uniform size (configuration 4).
+
+    workers > 1 generates maps in a spawn-started process pool (the result
+    is the same as with one process)."""
     cfg = SequenceConfig(MapSpec(256, 256, 64, 0.2), LidarSpec(128, 2048, 22.5), n_steps, 4.5)
-    scenes, yaws = [], []
-    for m in range(n_maps):
-        r = np.random.default_rng([seed, 0, m])
-        yaws.append(float(r.uniform(0, 2 * np.pi)))
-        scenes.append(make_sequence_scene(cfg, r, yaw0=yaws[-1]))
-    steps = []
-    for s in range(n_steps):
-        row = []
-        for m in range(n_maps):
-            r = np.random.default_rng([seed, 1, m, s])
-            size = int(math.floor(math.exp(r.uniform(math.log(lo), math.log(hi)))))
-            subset = np.sort(r.choice(cfg.lidar.n, size=size, replace=False))
-            t = s / cfg.rate_hz
-            veh, yaw, pitch = _trajectory_pose(scenes[m], cfg.speed, t, yaw0=yaws[m])
-            T = pose_matrix(veh, yaw, pitch)
-            row.append(scan_from_pose(scenes[m], cfg.lidar, T, veh, r, subset=subset, t=t))
-        steps.append(row)
+    jobs = [(seed, m, n_steps, lo, hi) for m in range(n_maps)]
+    if workers and workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            per_map = list(ex.map(_batched_map, jobs))
+    else:
+        per_map = [_batched_map(j) for j in jobs]
+    steps = [[per_map[m][s] for m in range(n_maps)] for s in range(n_steps)]
     return cfg, steps
 
 
