@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10, help="timed steps of the batched leg")
     ap.add_argument("--retune", action="store_true", help="ignore cached tuning and search again")
+    ap.add_argument("--no-served", action="store_true", help="skip the served leg")
+    ap.add_argument("--served-seconds", type=float, default=20.0, help="length of the replayed arrival stream")
     return ap.parse_args()
 
 
@@ -75,6 +77,17 @@ def make_inputs(rank: int):
 
 BATCHED_WORKLOAD = ("batched: {m} independent maps 256x256x64 @ 0.2 m, each its own terrain and trajectory, "
                     "scan sizes log-uniform in [8,192, 262,144] (subsets of a 128x2048 scan), 2 generated steps cycled")
+
+
+SERVED_WORKLOAD = ("served: 32 robots, mixed sensors (16/64/128 beams) and maps (128x128x32 @ 0.2 m, "
+                   "256x256x64 @ 0.2 m, 512x512x64 @ 0.1 m), exponential inter-arrival times (mean 100 ms), "
+                   "{s:g} s stream replayed in real time, each robot cycling a pool of 4 consecutive scans")
+
+
+def make_served_inputs(rank: int, seconds: float):
+    import synth
+    return synth.served_requests(n_robots=32, duration_s=seconds, pool=4, seed=synth.SEED_BASE + 5 + 1000 * rank,
+                                 workers=gen_workers())
 
 
 def make_batched_inputs(rank: int, n_maps: int):
@@ -316,6 +329,55 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+def run_served(args, gv, torch, inputs):
+    """The served workload: real-time replay with continuous batching (latency),
+    then all requests at once (capacity), batched vs one plain update per scan."""
+    from paper_2109_13176_gb300.serve import Server
+    robots, arrivals = inputs
+    specs = {i: r["map"] for i, r in enumerate(robots)}
+    scans = {i: [dict(points=torch.from_numpy(s.points).pin_memory(), T_ws=s.T_ws, vehicle_xyz=s.vehicle_xyz)
+                 for s in r["scans"]] for i, r in enumerate(robots)}
+    max_pts = sum(max(int(s["points"].shape[0]) for s in scans[i]) for i in scans)
+
+    def server():
+        return Server(specs, slots=2, max_batch_maps=len(robots), max_batch_points=max_pts, reserve_bytes=2 << 30)
+
+    srv = server()
+    rt = srv.run(arrivals, scans, realtime=True).summary()
+    srv.close()
+    srv = server()
+    sat = srv.run(arrivals, scans, realtime=False).summary()
+    srv.close()
+    # the plain path on the same requests: one update + extraction + readback per scan, in order
+    maps = {i: gv.VoxelMap(nx=sp.nx, ny=sp.ny, nz=sp.nz, res=sp.res, neg_max_px=int(math.ceil(2.0 / sp.res)))
+            for i, sp in specs.items()}
+    outs = {i: m.alloc_maps() for i, m in maps.items()}
+    host = {i: {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()} for i, o in outs.items()}
+    staging = torch.empty((max(int(s["points"].shape[0]) for i in scans for s in scans[i]), 3), device="cuda")
+    r0 = {i: m.stats()["rays_valid"] for i, m in maps.items()}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t, rid, k in arrivals:
+        sc = scans[rid][k]
+        n = int(sc["points"].shape[0])
+        view = staging[:n]
+        view.copy_(sc["points"], non_blocking=True)
+        maps[rid].update(sc["vehicle_xyz"], view, sc["T_ws"])
+        maps[rid].extract_maps(outs[rid])
+        for key, v in outs[rid].items():
+            host[rid][key].copy_(v, non_blocking=True)
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_rays = sum(m.stats()["rays_valid"] - r0[i] for i, m in maps.items())
+    for m in maps.values():
+        m.close()
+    return {"workload": SERVED_WORKLOAD.format(s=args.served_seconds), "robots": len(robots),
+            "requests": len(arrivals), "realtime": rt, "saturated": sat,
+            "plain_sequential": {"rays_per_s": plain_rays / plain_s, "wall_s": plain_s},
+            "capacity_speedup_vs_plain": sat["rays_per_s"] / (plain_rays / plain_s),
+            "slots": 2, "latency": "arrival to 2D products in pinned host memory (device event times)"}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -326,6 +388,7 @@ def main():
     # inputs first: the generator's process pool starts before any CUDA call
     cfg, scans = make_inputs(rank)
     batched_inputs = None if args.no_batched else make_batched_inputs(rank, args.batched_maps)
+    served_inputs = None if args.no_served else make_served_inputs(rank, args.served_seconds)
 
     import numpy as np
     import torch
@@ -437,6 +500,9 @@ def main():
     batched = None
     if batched_inputs is not None:
         batched = run_batched(args, gv, tune, torch, batched_inputs, flush, stream)
+    served = None
+    if served_inputs is not None:
+        served = run_served(args, gv, torch, served_inputs)
 
     peaks, peak_kind = read_peaks()
     red_peak = measure_red_peak(gv, torch)
@@ -486,6 +552,7 @@ def main():
         "tuning": {"seg_len": tuning[0], "march_block": tuning[1], "march_blocks_per_sm": tuning[2],
                    "search_us": tune_entry.get("us")},
         "batched": batched,
+        "served": served,
     }
     print(json.dumps(line), flush=True)
     gmap.close()

@@ -503,29 +503,41 @@ SERVED_MAPS = (MapSpec(128, 128, 32, 0.2), MapSpec(256, 256, 64, 0.2), MapSpec(5
 SERVED_LIDARS = (LidarSpec(16, 1024, 15.0), LidarSpec(64, 2048, 16.6), LidarSpec(128, 2048, 22.5))
 
 
+def _served_robot(args):
+    """Map spec, lidar and scan pool of one served robot."""
+    seed, i, pool = args
+    r = np.random.default_rng([seed, 0, i])
+    ms = SERVED_MAPS[int(r.integers(0, 3))]
+    ld = SERVED_LIDARS[int(r.integers(0, 3))]
+    speed = float(r.uniform(2.0, 12.0))
+    cfg = SequenceConfig(ms, ld, pool, speed, rough=0.1 if ms.res < 0.2 else 0.0)
+    yaw0 = float(r.uniform(0, 2 * np.pi))
+    sc = make_sequence_scene(cfg, r, yaw0=yaw0, extent=70.0)
+    scans = []
+    for k in range(pool):
+        t = k / 10.0
+        veh, yaw, pitch = _trajectory_pose(sc, speed, t, yaw0=yaw0)
+        T = pose_matrix(veh, yaw, pitch)
+        scans.append(scan_from_pose(sc, ld, T, veh, np.random.default_rng([seed, 1, i, k]), t=t))
+    return dict(map=ms, lidar=ld, scans=scans)
+
+
 def served_requests(n_robots: int = 32, duration_s: float = 60.0, pool: int = 4,
-                    seed: int = SEED_BASE + 5):
+                    seed: int = SEED_BASE + 5, workers: int = 0):
     """Robots (map spec, scan pool) and a time-ordered arrival list (configuration 5).
 
     Returns (robots, arrivals): robots[i] = dict(map=MapSpec, lidar=LidarSpec,
     scans=[Scan]*pool); arrivals = list of (t_arrival_s, robot, pool_index).
-    Robot i cycles through its pool of consecutive scans."""
-    robots = []
-    for i in range(n_robots):
-        r = np.random.default_rng([seed, 0, i])
-        ms = SERVED_MAPS[int(r.integers(0, 3))]
-        ld = SERVED_LIDARS[int(r.integers(0, 3))]
-        speed = float(r.uniform(2.0, 12.0))
-        cfg = SequenceConfig(ms, ld, pool, speed, rough=0.1 if ms.res < 0.2 else 0.0)
-        yaw0 = float(r.uniform(0, 2 * np.pi))
-        sc = make_sequence_scene(cfg, r, yaw0=yaw0)
-        scans = []
-        for k in range(pool):
-            t = k / 10.0
-            veh, yaw, pitch = _trajectory_pose(sc, speed, t, yaw0=yaw0)
-            T = pose_matrix(veh, yaw, pitch)
-            scans.append(scan_from_pose(sc, ld, T, veh, np.random.default_rng([seed, 1, i, k]), t=t))
-        robots.append(dict(map=ms, lidar=ld, scans=scans))
+    Robot i cycles through its pool of consecutive scans. workers > 1 builds
+    robots in a spawn-started process pool (same result)."""
+    jobs = [(seed, i, pool) for i in range(n_robots)]
+    if workers and workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            robots = list(ex.map(_served_robot, jobs))
+    else:
+        robots = [_served_robot(j) for j in jobs]
     arr = []
     r = np.random.default_rng([seed, 2])
     for i in range(n_robots):
