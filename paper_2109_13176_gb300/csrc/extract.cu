@@ -62,7 +62,7 @@ __device__ __forceinline__ void column_scalar(const MapState& s, const ExtractPa
                                               long long col) {
     const Geom g = p.g;
     const int lane = threadIdx.x & 31;
-    const int cx = (int)(col / g.ny), cy = (int)(col % g.ny);
+    const int cx = (int)((unsigned)col / (unsigned)g.ny), cy = (int)((unsigned)col % (unsigned)g.ny);
     int px = cx + g.rx;
     px -= (px >= g.nx) ? g.nx : 0;
     int py = cy + g.ry;
@@ -146,8 +146,8 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
     int cx = 0, cy = 0;
     size_t base = 0;
     if (have) {
-        cx = (int)(col / g.ny);
-        cy = (int)(col % g.ny);
+        cx = (int)((unsigned)col / (unsigned)g.ny);
+        cy = (int)((unsigned)col % (unsigned)g.ny);
         int px = cx + g.rx;
         px -= (px >= g.nx) ? g.nx : 0;
         int py = cy + g.ry;
@@ -241,80 +241,64 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
 
 constexpr int kTile = 16;
 constexpr int kPxBlock = 256;        // four cone-sweep warps and four plane-fit warps
-constexpr unsigned char kFar = 255;  // no ground within reach
+
+// Cone state of a cell, packed into one 64-bit key: the distance D of the
+// first ring holding ground in the high word, the lowest height on that ring
+// (as order-preserving bits) in the low word. Smaller key = nearer ring,
+// then lower height, so the state of a set of cones is their minimum key.
+constexpr unsigned long long kNoGround = ~0ull;
+
+__device__ __forceinline__ uint32_t height_key(float v) {
+    const uint32_t b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_height(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
 
 // One warp sweeps the cone recurrence of one direction over the tile. The
 // cone grows along +u (sgn = +1) or -u (sgn = -1), u = the tile's row axis
-// (x) when along_x, else its column axis (y). Ring 1 of a cell is the three
-// cells one step ahead; a cell with no ground on ring 1 takes 1 + the
-// smallest first-ring distance of those three cells, and the lowest height
-// among the ones at that distance. A cone whose ring leaves the grid along
-// u, or whose distance passes neg_max_px, has no value (kFar).
-// Writes the cone value of each tile-interior pixel to val (NaN: none).
+// (x) when along_x, else its column axis (y). With Q(c) = min(own key of c
+// (distance 0, its height) if c is defined, cone state of c), the cone
+// state of a cell is min over its three ring-1 cells n of Q(n), one ring
+// further (D + 1): ring d of a cell is the union of rings d - 1 of those
+// three cells. A cone whose ring-1 line lies outside the grid along u, or
+// whose distance passes neg_max_px, has no ground. Writes the cone value
+// (lowest height on the first ring with ground, NaN if none) of each
+// tile-interior pixel to val.
 __device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int gx0, int gy0, bool along_x,
-                                int sgn, unsigned char* Dbuf, float* Vbuf, float* val) {
+                                int sgn, unsigned long long* Qbuf, float* val) {
     const int lane = threadIdx.x & 31;
     const int nmaj = along_x ? p.g.nx : p.g.ny;
     const int g0 = along_x ? gx0 : gy0;  // global coordinate of tile row 0 along u
     const int first = sgn > 0 ? W - 1 : 0;
     const int last = sgn > 0 ? R : R + kTile - 1;
     const int nsteps = sgn > 0 ? first - last + 1 : last - first + 1;
+    const unsigned long long dmax = (unsigned long long)p.neg_max_px << 32;
     const float qnan = __int_as_float(0x7fffffff);
     for (int st = 0; st < nsteps; ++st) {
         const int u = first - sgn * st;
-        unsigned char* Dcur = Dbuf + (st & 1) * W;
-        float* Vcur = Vbuf + (st & 1) * W;
-        const unsigned char* Dprev = Dbuf + ((st + 1) & 1) * W;
-        const float* Vprev = Vbuf + ((st + 1) & 1) * W;
-        const int un = u + sgn;   // the ring-1 line
+        unsigned long long* Qcur = Qbuf + (st & 1) * W;
+        const unsigned long long* Qprev = Qbuf + ((st + 1) & 1) * W;
+        const int un = u + sgn;   // the ring-1 line (the previous step's)
         const int gun = g0 + un;  // its global coordinate
         const bool ring_ok = gun >= 0 && gun < nmaj && un >= 0 && un < W;
         for (int v = lane; v < W; v += 32) {
-            unsigned char D = kFar;
-            float V = 0.f;
+            unsigned long long c = kNoGround;
             if (ring_ok) {
-                float m = __int_as_float(0x7f800000);
-                bool any = false;
-#pragma unroll
-                for (int dv = -1; dv <= 1; ++dv) {
-                    const int vv = v + dv;
-                    if (vv < 0 || vv >= W) continue;
-                    const float hv = along_x ? Hs[un * W + vv] : Hs[vv * W + un];
-                    if (!isnan(hv)) {
-                        m = fminf(m, hv);
-                        any = true;
-                    }
-                }
-                if (any) {
-                    D = 1;
-                    V = m;
-                } else if (st > 0) {
-                    unsigned char dmin = kFar;
-                    float mv = __int_as_float(0x7f800000);
-#pragma unroll
-                    for (int dv = -1; dv <= 1; ++dv) {
-                        const int vv = v + dv;
-                        if (vv < 0 || vv >= W) continue;
-                        const unsigned char dd = Dprev[vv];
-                        const float vvv = Vprev[vv];
-                        if (dd < dmin) {
-                            dmin = dd;
-                            mv = vvv;
-                        } else if (dd == dmin) {
-                            mv = fminf(mv, vvv);
-                        }
-                    }
-                    if (dmin != kFar && (int)dmin + 1 <= p.neg_max_px) {
-                        D = (unsigned char)(dmin + 1);
-                        V = mv;
-                    }
-                }
+                unsigned long long q = Qprev[v];
+                if (v > 0) q = min(q, Qprev[v - 1]);
+                if (v + 1 < W) q = min(q, Qprev[v + 1]);
+                if (q != kNoGround && (q >> 32) < dmax >> 32) c = q + (1ull << 32);
             }
-            Dcur[v] = D;
-            Vcur[v] = V;
+            const float h = along_x ? Hs[u * W + v] : Hs[v * W + u];
+            const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
+            Qcur[v] = min(own, c);
             const int iu = u - R, iv = v - R;
             if (iu >= 0 && iu < kTile && iv >= 0 && iv < kTile)
-                val[along_x ? iu * kTile + iv : iv * kTile + iu] = D != kFar ? V : qnan;
+                val[along_x ? iu * kTile + iv : iv * kTile + iu] =
+                    c != kNoGround ? key_height((uint32_t)c) : qnan;
         }
         __syncwarp();
     }
@@ -386,10 +370,9 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     const int R = max(p.neg_max_px, r);
     const int W = kTile + 2 * R;
     const int warp = threadIdx.x >> 5;
-    float* Hs = smem;                                   // W * W heights, NaN outside the grid
+    unsigned long long* Qbufs = reinterpret_cast<unsigned long long*>(smem);  // 4 * 2W cone keys
+    float* Hs = smem + 16 * W;                          // W * W heights, NaN outside the grid
     float* vals = Hs + W * W;                           // 4 * kTile^2 cone values
-    float* Vbufs = vals + 4 * kTile * kTile;            // 4 * 2W
-    unsigned char* Dbufs = reinterpret_cast<unsigned char*>(Vbufs + 8 * W);  // 4 * 2W
     const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
 
@@ -402,8 +385,8 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
 
     if (warp < 4) {
         if (flags)
-            cone_sweep_warp(p, Hs, W, R, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Dbufs + warp * 2 * W,
-                            Vbufs + warp * 2 * W, vals + warp * kTile * kTile);
+            cone_sweep_warp(p, Hs, W, R, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
+                            vals + warp * kTile * kTile);
     } else {
         for (int t = threadIdx.x - 128; t < kTile * kTile; t += 128) {
             const int li = t / kTile, lj = t % kTile;
@@ -506,14 +489,14 @@ __global__ void __launch_bounds__(kPxBlock, 4) k_slope_negative_batch(BatchTable
         const BatchExtract& ex = t.ex[m];
         const long long lt = u - t.tile_prefix[m];
         const int tiles_y = (ex.p.g.ny + kTile - 1) / kTile;
-        tile_body(ex.p, ex.height, ex.slope, ex.rough, ex.flags, (int)(lt / tiles_y) * kTile,
-                  (int)(lt % tiles_y) * kTile, smem);
+        tile_body(ex.p, ex.height, ex.slope, ex.rough, ex.flags, (int)((unsigned)lt / (unsigned)tiles_y) * kTile,
+                  (int)((unsigned)lt % (unsigned)tiles_y) * kTile, smem);
     }
 }
 
 size_t slope_negative_smem_halo(int R) {
     const int W = kTile + 2 * R;
-    return sizeof(float) * ((size_t)W * W + 4 * kTile * kTile + 8 * (size_t)W) + 8 * (size_t)W;
+    return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * kTile * kTile);
 }
 
 size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_halo(tile_halo(p)); }

@@ -563,12 +563,12 @@ __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_
     const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
     int cx, cy;
     if (u < n_xslab) {
-        const int k = (int)(u / g.ny);
+        const int k = (int)((unsigned)u / (unsigned)g.ny);
         cx = dx > 0 ? g.nx - dx + k : k;
-        cy = (int)(u % g.ny);
+        cy = (int)((unsigned)u % (unsigned)g.ny);
     } else {
         const long long w = u - n_xslab;
-        const int k = (int)(w / ady), l = (int)(w % ady);
+        const int k = (int)((unsigned)w / (unsigned)ady), l = (int)((unsigned)w % (unsigned)ady);
         cx = (dx > 0 ? 0 : adx) + k;
         cy = dy > 0 ? g.ny - dy + l : l;
     }
@@ -581,8 +581,8 @@ __global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
     const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int wy = g.ny - ady;
     if (w >= (long long)(g.nx - adx) * wy) return;
-    const int cx = (dx > 0 ? 0 : adx) + (int)(w / wy);
-    const int cy = (dy > 0 ? 0 : ady) + (int)(w % wy);
+    const int cx = (dx > 0 ? 0 : adx) + (int)((unsigned)w / (unsigned)wy);
+    const int cy = (dy > 0 ? 0 : ady) + (int)((unsigned)w % (unsigned)wy);
     const uint32_t base = column_base(g, cx, cy);
     const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
     for (int cz = z0; cz < z1; ++cz) {
@@ -642,12 +642,12 @@ __global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
         if (lu < n_cols) {
             int cx, cy;
             if (lu < n_xslab) {
-                const int k = (int)(lu / g.ny);
+                const int k = (int)((unsigned)lu / (unsigned)g.ny);
                 cx = dx > 0 ? g.nx - dx + k : k;
-                cy = (int)(lu % g.ny);
+                cy = (int)((unsigned)lu % (unsigned)g.ny);
             } else {
                 const long long w = lu - n_xslab;
-                const int k = (int)(w / ady), l = (int)(w % ady);
+                const int k = (int)((unsigned)w / (unsigned)ady), l = (int)((unsigned)w % (unsigned)ady);
                 cx = (dx > 0 ? 0 : adx) + k;
                 cy = dy > 0 ? g.ny - dy + l : l;
             }
@@ -658,8 +658,8 @@ __global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
             const int wy = g.ny - ady;
             const long long w = (lu - n_cols) * 32 + lane;
             if (w >= (long long)(g.nx - adx) * wy) continue;
-            const int cx = (dx > 0 ? 0 : adx) + (int)(w / wy);
-            const int cy = (dy > 0 ? 0 : ady) + (int)(w % wy);
+            const int cx = (dx > 0 ? 0 : adx) + (int)((unsigned)w / (unsigned)wy);
+            const int cy = (dy > 0 ? 0 : ady) + (int)((unsigned)w % (unsigned)wy);
             const uint32_t base = column_base(g, cx, cy);
             const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
             for (int cz = z0; cz < z1; ++cz) {
