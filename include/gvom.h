@@ -227,10 +227,13 @@ GVOM_API int gvom_extract_voxels(struct gvom_map* map, uint32_t* hits_dev, uint3
                         gvom_stream_t stream);
 
 /* Reads the counters. Synchronises with the map's last enqueued work
- * (device-wide synchronisation). */
+ * (device-wide synchronisation). Returns GVOM_ERR_TIMEOUT (with *out still
+ * filled) if, since creation or the last gvom_reset_stats, a bounded wait
+ * inside one of the map's kernels gave up; that kernel's outputs are then
+ * incomplete. */
 GVOM_API int gvom_get_stats(struct gvom_map* map, gvom_stats* out);
 
-/* Zeroes the counters. Stream-ordered. */
+/* Zeroes the counters and the timeout status. Stream-ordered. */
 GVOM_API int gvom_reset_stats(struct gvom_map* map, gvom_stream_t stream);
 
 /* ---- Batched update of many maps ---------------------------------------

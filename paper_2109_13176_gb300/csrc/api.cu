@@ -368,7 +368,7 @@ int gvom_get_stats(gvom_map* m, gvom_stats* out) {
     out->rays_valid = (int64_t)c[gvom::kRaysValid];
     out->hits_in_window = (int64_t)c[gvom::kHitsInWindow];
     out->pass_visits = (int64_t)c[gvom::kPassVisits];
-    return GVOM_OK;
+    return c[gvom::kStatus] != 0 ? GVOM_ERR_TIMEOUT : GVOM_OK;
 }
 
 int gvom_reset_stats(gvom_map* m, gvom_stream_t stream) {

@@ -291,7 +291,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         h.col_prefix[m] = col_tasks;
         col_tasks += ((long long)g.nx * g.ny + gvom::kColTask - 1) / gvom::kColTask;
         h.tile_prefix[m] = tiles;
-        tiles += gvom::tiles_of(g);
+        tiles += gvom::tiles_of(ex.p);
     }
     h.shift_prefix[B] = shift_total;
     h.ray_prefix[B] = ray_blocks;

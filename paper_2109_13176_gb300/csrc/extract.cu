@@ -34,19 +34,30 @@ __device__ __forceinline__ float density_of(unsigned long long H, unsigned long 
 }
 
 // The oracle's test lo <= (double)a - (double)b <= hi for floats a, b and
-// float bounds: decided on the FP32 difference unless that lies within a
-// relative 2^-20 of a bound (where FP32 and FP64 rounding could disagree),
-// and there by the FP64 difference.
-__device__ __forceinline__ bool in_band(float a, float b, float lo, float hi) {
-    const float d = __fsub_rn(a, b);
+// float bounds. The FP32 difference decides unless it lies within a
+// relative 2^-20 of a bound (where FP32 and FP64 rounding could disagree);
+// there the FP64 difference decides. Band holds the four edges of those
+// ambiguous zones, computed once.
+struct Band {
+    float lo, hi;                    // the band
+    float lo_m, lo_p, hi_m, hi_p;    // lo -+ tl, hi -+ th
+};
+
+__device__ __forceinline__ Band make_band(float lo, float hi) {
     const float tl = fabsf(lo) * 9.5367432e-7f + 1e-30f;
     const float th = fabsf(hi) * 9.5367432e-7f + 1e-30f;
-    if (fabsf(d - lo) <= tl || fabsf(d - hi) <= th) {
-        const double e = __dsub_rn((double)a, (double)b);
-        return (double)lo <= e && e <= (double)hi;
-    }
-    return lo <= d && d <= hi;
+    return Band{lo, hi, lo - tl, lo + tl, hi - th, hi + th};
 }
+
+__device__ __forceinline__ bool in_band(float a, float b, const Band& B) {
+    const float d = __fsub_rn(a, b);
+    if (d < B.lo_m || d > B.hi_p) return false;   // clearly outside
+    if (d > B.lo_p && d < B.hi_m) return true;    // clearly inside
+    const double e = __dsub_rn((double)a, (double)b);
+    return (double)B.lo <= e && e <= (double)B.hi;
+}
+
+__device__ __forceinline__ bool in_band(float a, float b, float lo, float hi) { return in_band(a, b, make_band(lo, hi)); }
 
 // The oracle's test (double)hi - (double)lo > thresh, filtered the same way.
 __device__ __forceinline__ bool exceeds(float hi, float lo, float thresh) {
@@ -140,7 +151,7 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
     const int sub = lane % LPC;                  // lane within the column group
     const unsigned gmask = (LPC == 32) ? 0xffffffffu : (((1u << LPC) - 1u) << (lane - sub));
     const int nv = g.nz >> 2;  // 16-byte vectors per run
-    const float lof = p.obs_min_h, hif = p.obs_max_h;
+    const Band band = make_band(p.obs_min_h, p.obs_max_h);
     const long long col = colb + (lane / LPC);
     const bool have = col < col_end;
     int cx = 0, cy = 0;
@@ -188,7 +199,7 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
             bool in[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                in[k] = hs[k] != 0u && in_band(ms[k], h, lof, hif);
+                in[k] = hs[k] != 0u && in_band(ms[k], h, band);
                 need |= in[k];
             }
             if (need) {
@@ -239,8 +250,197 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
         columns_step<LPC>(s, p, height, density, flags, colb, ncols);
 }
 
-constexpr int kTile = 16;
-constexpr int kPxBlock = 256;        // four cone-sweep warps and four plane-fit warps
+// ---- TMA-staged column pass (nz % 4 == 0) ----------------------------------
+//
+// The map state is column-major (z fastest), so C consecutive physical
+// columns of hits (and of lowest returns) are one contiguous run of
+// C * nz * 4 bytes. One thread per block streams such runs into a ring of
+// shared-memory stages with 1D bulk copies (cp.async.bulk, completion on an
+// mbarrier per stage), kStages chunks ahead; all warps reduce the chunk in
+// place, LPC = 8 lanes per column. Passes are read from global memory only
+// for the voxels of the obstacle band. Every mbarrier wait is bounded; a
+// wait that gives up sets the map's status word and the block returns after
+// draining the copies it issued. Used for nz % 4 == 0 and nz <= 256 (three
+// stages of 2 x 32 columns fit shared memory; each stage's transaction count
+// stays below the mbarrier's 2^20 bytes).
+
+constexpr int kTmaCols = 32;      // columns per chunk
+constexpr int kTmaStages = 3;
+constexpr int kTmaBlock = 256;
+constexpr unsigned kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Waits for phase `parity` of the barrier, at most kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned i = 0; i < kSpinLimit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 2 * kTmaCols * nz * sizeof(float); }
+
+// Starts the copies of chunk `chunk` into `stage`.
+__device__ __forceinline__ void tma_issue(const MapState& s, int nz, long long ncols, long long chunk, int stage,
+                                          unsigned long long* bars, uint32_t* hb, float* mb) {
+    const long long c0 = chunk * kTmaCols;
+    const long long cols = ncols - c0 < kTmaCols ? ncols - c0 : kTmaCols;
+    const unsigned bytes = (unsigned)(cols * nz * 4);
+    mbar_expect_tx(&bars[stage], 2u * bytes);
+    bulk_load(hb + (size_t)stage * kTmaCols * nz, s.hits + c0 * nz, bytes, &bars[stage]);
+    bulk_load(mb + (size_t)stage * kTmaCols * nz, s.minz + c0 * nz, bytes, &bars[stage]);
+}
+
+__global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
+                                                            float* __restrict__ density,
+                                                            uint8_t* __restrict__ flags) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ int s_fail;
+    const Geom g = p.g;
+    const int nz = g.nz, nv = nz >> 2;
+    const long long ncols = (long long)g.nx * g.ny;
+    const long long nchunks = (ncols + kTmaCols - 1) / kTmaCols;
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm);
+    uint32_t* hb = reinterpret_cast<uint32_t*>(sm + 128);
+    float* mb = reinterpret_cast<float*>(hb + (size_t)kTmaStages * kTmaCols * nz);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int sub = lane & 7;                      // lane within the column's 8-lane group
+    const Band band = make_band(p.obs_min_h, p.obs_max_h);
+
+    if (tid == 0) {
+        for (int st = 0; st < kTmaStages; ++st) mbar_init(&bars[st], 1);
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int st = 0; st < kTmaStages; ++st) {
+            const long long c = blockIdx.x + (long long)st * gridDim.x;
+            if (c < nchunks) tma_issue(s, nz, ncols, c, st, bars, hb, mb);
+        }
+
+    int k = 0;
+    for (;; ++k) {
+        const long long c = blockIdx.x + (long long)k * gridDim.x;
+        if (c >= nchunks) break;
+        const int st = k % kTmaStages;
+        if (!mbar_wait(&bars[st], (unsigned)((k / kTmaStages) & 1))) s_fail = 1;
+        __syncthreads();
+        if (s_fail) break;
+        const uint32_t* hst = hb + (size_t)st * kTmaCols * nz;
+        const float* mst = mb + (size_t)st * kTmaCols * nz;
+        const long long c0 = c * kTmaCols;
+        // 8 warps x 4 columns = the chunk's 32 columns
+        const int j = warp * 4 + (lane >> 3);
+        const long long pc = c0 + j;                 // physical column
+        const bool have = pc < ncols;
+        const uint4* hv4 = reinterpret_cast<const uint4*>(hst + (size_t)j * nz);
+        const float4* mv4 = reinterpret_cast<const float4*>(mst + (size_t)j * nz);
+        float h = __int_as_float(0x7f800000);
+        bool any = false;
+        if (have)
+            for (int v = sub; v < nv; v += 8) {
+                const uint4 a = hv4[v];
+                const float4 b = mv4[v];
+                if (a.x) { h = fminf(h, b.x); any = true; }
+                if (a.y) { h = fminf(h, b.y); any = true; }
+                if (a.z) { h = fminf(h, b.z); any = true; }
+                if (a.w) { h = fminf(h, b.w); any = true; }
+            }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
+        const unsigned gm = 0xffu << (lane & 24);
+        const bool col_any = (__ballot_sync(0xffffffffu, any) & gm) != 0u;
+        unsigned long long H = 0, M = 0;
+        bool inband = false;
+        if (have && col_any)
+            for (int v = sub; v < nv; v += 8) {
+                const uint4 a = hv4[v];
+                const float4 b = mv4[v];
+                const uint32_t hs[4] = {a.x, a.y, a.z, a.w};
+                const float ms[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (hs[q] != 0u && in_band(ms[q], h, band)) {
+                        H += hs[q];
+                        M += s.passes[pc * nz + 4 * v + q];
+                        inband = true;
+                    }
+            }
+        if (__ballot_sync(0xffffffffu, inband)) {
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                H += __shfl_xor_sync(0xffffffffu, H, o);
+                M += __shfl_xor_sync(0xffffffffu, M, o);
+            }
+        }
+        if (have && sub == 0) {
+            // window coordinates of the physical column
+            const int px = (int)((unsigned)pc / (unsigned)g.ny), py = (int)((unsigned)pc % (unsigned)g.ny);
+            int cx = px - g.rx;
+            cx += cx < 0 ? g.nx : 0;
+            int cy = py - g.ry;
+            cy += cy < 0 ? g.ny : 0;
+            const size_t o = (size_t)cx * g.ny + cy;
+            if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
+            uint8_t f = 0;
+            float dens = 0.0f;
+            if (H > 0) {
+                dens = density_of(H, H + M);
+                const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
+                f = hard ? 3 : 5;
+            }
+            if (density) density[o] = dens;
+            if (flags) flags[o] = f;
+        }
+        __syncthreads();  // every warp is done with this stage
+        if (tid == 0) {
+            const long long c2 = c + (long long)kTmaStages * gridDim.x;
+            if (c2 < nchunks) tma_issue(s, nz, ncols, c2, st, bars, hb, mb);
+        }
+    }
+    if (s_fail && tid == 0) {
+        // drain the copies this block issued and has not consumed, then report
+        for (int q = k; q < k + kTmaStages; ++q) {
+            const long long c = blockIdx.x + (long long)q * gridDim.x;
+            if (c >= nchunks) break;
+            mbar_wait(&bars[q % kTmaStages], (unsigned)((q / kTmaStages) & 1));
+        }
+        atomicOr(s.counters + kStatus, 1ull);
+    }
+}
+
+constexpr int kMaxTile = 16;
+
+// Tile edge of the pixel pass: 8 for halos up to 12 pixels (more blocks,
+// one sweep step per lane), else 16 (less halo overhead).
+__host__ __device__ __forceinline__ int tile_edge(const ExtractParams& p) {
+    const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
+    return R <= 12 ? 8 : kMaxTile;
+}
+constexpr int kPxBlock = 128;        // four warps: all fit planes, then each sweeps one cone direction
 
 // Cone state of a cell, packed into one 64-bit key: the distance D of the
 // first ring holding ground in the high word, the lowest height on that ring
@@ -267,13 +467,13 @@ __device__ __forceinline__ float key_height(uint32_t k) {
 // whose distance passes neg_max_px, has no ground. Writes the cone value
 // (lowest height on the first ring with ground, NaN if none) of each
 // tile-interior pixel to val.
-__device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int gx0, int gy0, bool along_x,
-                                int sgn, unsigned long long* Qbuf, float* val) {
+__device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int tile, int gx0, int gy0,
+                                bool along_x, int sgn, unsigned long long* Qbuf, float* val) {
     const int lane = threadIdx.x & 31;
     const int nmaj = along_x ? p.g.nx : p.g.ny;
     const int g0 = along_x ? gx0 : gy0;  // global coordinate of tile row 0 along u
     const int first = sgn > 0 ? W - 1 : 0;
-    const int last = sgn > 0 ? R : R + kTile - 1;
+    const int last = sgn > 0 ? R : R + tile - 1;
     const int nsteps = sgn > 0 ? first - last + 1 : last - first + 1;
     const unsigned long long dmax = (unsigned long long)p.neg_max_px << 32;
     const float qnan = __int_as_float(0x7fffffff);
@@ -296,8 +496,8 @@ __device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, 
             const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
             Qcur[v] = min(own, c);
             const int iu = u - R, iv = v - R;
-            if (iu >= 0 && iu < kTile && iv >= 0 && iv < kTile)
-                val[along_x ? iu * kTile + iv : iv * kTile + iu] =
+            if (iu >= 0 && iu < tile && iv >= 0 && iv < tile)
+                val[along_x ? iu * tile + iv : iv * tile + iu] =
                     c != kNoGround ? key_height((uint32_t)c) : qnan;
         }
         __syncwarp();
@@ -359,20 +559,21 @@ __device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* H
     ro = sse / (float)n;
 }
 
-// Block: warps 0-3 sweep the four cones (+x, -x, +y, -y) while warps 4-7
-// fit the planes of the defined pixels; then every thread combines the
-// cone values of one pixel.
+// One tile of tile x tile pixels per block of four warps: load the tile and
+// its halo, fit the planes of the defined pixels, then warp w sweeps cone w
+// (+x, -x, +y, -y), and every pixel combines its four cone values.
 __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* __restrict__ height,
                                           float* __restrict__ slope, float* __restrict__ rough,
-                                          uint8_t* __restrict__ flags, int tx0, int ty0, float* smem) {
+                                          uint8_t* __restrict__ flags, int tx0, int ty0, int tile, float* smem) {
     const int nx = p.g.nx, ny = p.g.ny;
     const int r = p.slope_n / 2;
     const int R = max(p.neg_max_px, r);
-    const int W = kTile + 2 * R;
+    const int W = tile + 2 * R;
     const int warp = threadIdx.x >> 5;
+    const int tt = tile * tile;
     unsigned long long* Qbufs = reinterpret_cast<unsigned long long*>(smem);  // 4 * 2W cone keys
     float* Hs = smem + 16 * W;                          // W * W heights, NaN outside the grid
-    float* vals = Hs + W * W;                           // 4 * kTile^2 cone values
+    float* vals = Hs + W * W;                           // 4 * tile^2 cone values
     const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
 
@@ -383,57 +584,56 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     }
     __syncthreads();
 
-    if (warp < 4) {
-        if (flags)
-            cone_sweep_warp(p, Hs, W, R, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
-                            vals + warp * kTile * kTile);
-    } else {
-        for (int t = threadIdx.x - 128; t < kTile * kTile; t += 128) {
-            const int li = t / kTile, lj = t % kTile;
-            const int cx = tx0 + li, cy = ty0 + lj;
-            if (cx >= nx || cy >= ny) continue;
-            const int ci = li + R, cj = lj + R;
-            const float h0 = Hs[ci * W + cj];
-            float sl = qnan, ro = qnan;
-            if (!isnan(h0)) {
-                if (r == 2)
-                    plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
-                else if (r == 1)
-                    plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
-                else
-                    plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
-            }
-            const size_t o = (size_t)cx * ny + cy;
-            if (slope) slope[o] = sl;
-            if (rough) rough[o] = ro;
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; flags && t < kTile * kTile; t += blockDim.x) {
-        const int li = t / kTile, lj = t % kTile;
+    for (int t = threadIdx.x; t < tt; t += blockDim.x) {
+        const int li = t / tile, lj = t % tile;
         const int cx = tx0 + li, cy = ty0 + lj;
         if (cx >= nx || cy >= ny) continue;
-        if (!isnan(Hs[(li + R) * W + (lj + R)])) continue;
-        int nf = 0;
-        float lo = 0.f, hi = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float v = vals[c * kTile * kTile + t];
-            if (isnan(v)) continue;
-            lo = nf ? fminf(lo, v) : v;
-            hi = nf ? fmaxf(hi, v) : v;
-            nf += 1;
+        const int ci = li + R, cj = lj + R;
+        const float h0 = Hs[ci * W + cj];
+        float sl = qnan, ro = qnan;
+        if (!isnan(h0)) {
+            if (r == 2)
+                plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
+            else if (r == 1)
+                plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
+            else
+                plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
         }
-        if (nf >= 2 && exceeds(hi, lo, p.neg_thresh)) flags[(size_t)cx * ny + cy] |= 8u;
+        const size_t o = (size_t)cx * ny + cy;
+        if (slope) slope[o] = sl;
+        if (rough) rough[o] = ro;
+    }
+    if (flags) {
+        cone_sweep_warp(p, Hs, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
+                        vals + warp * tt);
+        __syncthreads();
+        for (int t = threadIdx.x; t < tt; t += blockDim.x) {
+            const int li = t / tile, lj = t % tile;
+            const int cx = tx0 + li, cy = ty0 + lj;
+            if (cx >= nx || cy >= ny) continue;
+            if (!isnan(Hs[(li + R) * W + (lj + R)])) continue;
+            int nf = 0;
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float v = vals[c * tt + t];
+                if (isnan(v)) continue;
+                lo = nf ? fminf(lo, v) : v;
+                hi = nf ? fmaxf(hi, v) : v;
+                nf += 1;
+            }
+            if (nf >= 2 && exceeds(hi, lo, p.neg_thresh)) flags[(size_t)cx * ny + cy] |= 8u;
+        }
     }
     __syncthreads();  // the caller may reuse the shared arrays for its next tile
 }
 
-__global__ void __launch_bounds__(kPxBlock, 4)
+__global__ void __launch_bounds__(kPxBlock, 8)
     k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
                      float* __restrict__ rough, uint8_t* __restrict__ flags) {
     extern __shared__ float smem[];
-    tile_body(p, height, slope, rough, flags, blockIdx.y * kTile, blockIdx.x * kTile, smem);
+    const int tile = tile_edge(p);
+    tile_body(p, height, slope, rough, flags, blockIdx.y * tile, blockIdx.x * tile, tile, smem);
 }
 
 // ---- batched maps ----------------------------------------------------------
@@ -480,7 +680,7 @@ __global__ void __launch_bounds__(kColBlock) k_columns_batch(BatchTables t) {
 }
 
 // Plane-fit / cone pass of all maps: a persistent grid over pixel tiles.
-__global__ void __launch_bounds__(kPxBlock, 4) k_slope_negative_batch(BatchTables t) {
+__global__ void __launch_bounds__(kPxBlock, 8) k_slope_negative_batch(BatchTables t) {
     extern __shared__ float smem[];
     const int B = t.hdr->B;
     const long long total = t.hdr->tiles;
@@ -488,15 +688,17 @@ __global__ void __launch_bounds__(kPxBlock, 4) k_slope_negative_batch(BatchTable
         const int m = find_map_x(t.tile_prefix, B, u);
         const BatchExtract& ex = t.ex[m];
         const long long lt = u - t.tile_prefix[m];
-        const int tiles_y = (ex.p.g.ny + kTile - 1) / kTile;
-        tile_body(ex.p, ex.height, ex.slope, ex.rough, ex.flags, (int)((unsigned)lt / (unsigned)tiles_y) * kTile,
-                  (int)((unsigned)lt % (unsigned)tiles_y) * kTile, smem);
+        const int tile = tile_edge(ex.p);
+        const int tiles_y = (ex.p.g.ny + tile - 1) / tile;
+        tile_body(ex.p, ex.height, ex.slope, ex.rough, ex.flags, (int)((unsigned)lt / (unsigned)tiles_y) * tile,
+                  (int)((unsigned)lt % (unsigned)tiles_y) * tile, tile, smem);
     }
 }
 
 size_t slope_negative_smem_halo(int R) {
-    const int W = kTile + 2 * R;
-    return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * kTile * kTile);
+    const int tile = R <= 12 ? 8 : kMaxTile;
+    const int W = tile + 2 * R;
+    return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * tile * tile);
 }
 
 size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_halo(tile_halo(p)); }
@@ -533,7 +735,10 @@ int sm_count() {
 
 int tile_halo(const ExtractParams& p) { return p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2; }
 
-long long tiles_of(const Geom& g) { return (long long)((g.nx + kTile - 1) / kTile) * ((g.ny + kTile - 1) / kTile); }
+long long tiles_of(const ExtractParams& p) {
+    const int t = tile_edge(p);
+    return (long long)((p.g.nx + t - 1) / t) * ((p.g.ny + t - 1) / t);
+}
 
 cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st) {
     (void)max_maps;
@@ -548,13 +753,24 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
         if (e != cudaSuccess) return e;
     }
     count_launch();
-    k_slope_negative_batch<<<(unsigned)(sms * 4), kPxBlock, smem, st>>>(t);
+    k_slope_negative_batch<<<(unsigned)(sms * 8), kPxBlock, smem, st>>>(t);
     return cudaGetLastError();
 }
 
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density, uint8_t* flags,
                            cudaStream_t st) {
     const long long cols = (long long)p.g.nx * p.g.ny;
+    if ((p.g.nz & 3) == 0 && p.g.nz <= 256 && s.counters != nullptr) {
+        const size_t smem = columns_tma_smem(p.g.nz);
+        cudaError_t e = cudaFuncSetAttribute(k_columns_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const long long chunks = (cols + kTmaCols - 1) / kTmaCols;
+        long long blocks = (long long)sm_count() * 4;
+        if (blocks > chunks) blocks = chunks;
+        count_launch();
+        k_columns_tma<<<(unsigned)blocks, kTmaBlock, smem, st>>>(s, p, height, density, flags);
+        return cudaGetLastError();
+    }
     count_launch();
     if ((p.g.nz & 3) != 0) {
         const long long blocks = (cols * 32 + kColBlock - 1) / kColBlock;
@@ -584,7 +800,8 @@ cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, f
             cudaFuncSetAttribute(k_slope_negative, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((p.g.ny + kTile - 1) / kTile, (p.g.nx + kTile - 1) / kTile);
+    const int tile = tile_edge(p);
+    dim3 grid((p.g.ny + tile - 1) / tile, (p.g.nx + tile - 1) / tile);
     count_launch();
     k_slope_negative<<<grid, kPxBlock, smem, st>>>(p, height, slope, rough, flags);
     return cudaGetLastError();

@@ -26,7 +26,9 @@ struct MapState {
     unsigned long long* counters;  // kCounters entries
 };
 
-enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3, kCounters = 4 };
+// counters[kStatus] != 0: a bounded device wait of one of the map's kernels
+// gave up (reported by gvom_get_stats as GVOM_ERR_TIMEOUT).
+enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3, kStatus = 4, kCounters = 5 };
 
 // Per-scan scratch of the two-phase ingest, owned by the map: one record
 // per point (quantised endpoint and its number of traversal segments), the
@@ -118,7 +120,7 @@ struct BatchTables {
 
 constexpr int kColTask = 64;       // columns per warp task of the batched column pass
 long long shift_units(const Geom& g, const int d[3], int whole);
-long long tiles_of(const Geom& g);
+long long tiles_of(const ExtractParams& p);
 int tile_halo(const ExtractParams& p);
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
                                 const MarchShape& shape, cudaStream_t st);

@@ -28,7 +28,6 @@ namespace gvom {
 namespace {
 
 constexpr int kRaysBlock = 256;
-constexpr double kQLim = 1073741824.0;  // 2^30: quantised coordinates stay below this magnitude
 
 __device__ __forceinline__ bool in_window(const Geom& g, int cx, int cy, int cz) {
     return (unsigned)cx < (unsigned)g.nx && (unsigned)cy < (unsigned)g.ny && (unsigned)cz < (unsigned)g.nz;
@@ -65,12 +64,30 @@ __device__ __forceinline__ double xform_row(const double* T, double px, double p
 }
 
 // Quantise a map-frame coordinate to 1/256 voxel from the window origin:
-// q = round-half-even(fma(w, S, -256 origin)) with S = 256 (1 / res).
+// q = round-half-even(fma(w, S, -256 origin)) with S = 256 (1 / res),
+// valid iff |fma(...)| < 2^30. The bound is tested on the exponent bits
+// (|s| < 2^30 iff the high word of |s| is below that of 2^30; NaN and
+// infinities fail), so no FP64 compare is issued.
 __device__ __forceinline__ bool quantise(double w, double S, double neg_o256, int* q) {
     const double s = __fma_rn(w, S, neg_o256);
-    if (!(fabs(s) < kQLim)) return false;
+    if (((unsigned)__double2hiint(s) & 0x7fffffffu) >= 0x41d00000u) return false;
     *q = (int)__double2ll_rn(s);
     return true;
+}
+
+// The range filter 0 < r2 <= r2max with r2 = fma(pz, pz, fma(py, py, px px))
+// in FP64 (the oracle's). r2 > 0 iff some component is non-zero (squares of
+// floats cannot underflow in FP64). The FP32 sum of squares decides unless
+// it lies within a relative 2^-20 of r2max (FP32 error <= 3 * 2^-24), where
+// the FP64 value decides.
+__device__ __forceinline__ bool in_range(float fx, float fy, float fz, float r2max_lo, float r2max_hi, double r2max) {
+    if (fx == 0.0f && fy == 0.0f && fz == 0.0f) return false;
+    const float r2f = __fmaf_rn(fz, fz, __fmaf_rn(fy, fy, __fmul_rn(fx, fx)));
+    if (r2f < r2max_lo) return true;
+    if (r2f > r2max_hi) return false;
+    const double px = fx, py = fy, pz = fz;
+    const double r2 = __fma_rn(pz, pz, __fma_rn(py, py, __dmul_rn(px, px)));
+    return r2 <= r2max;
 }
 
 // The sensor's quantised position, computed once per block and shared.
@@ -169,10 +186,11 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
             fy = __ldg(p + 1);
             fz = __ldg(p + 2);
         }
-        if (isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok) {
+        const float r2max_f = (float)a.r2max;
+        if (isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok &&
+            in_range(fx, fy, fz, r2max_f * (1.0f - 9.5367432e-7f), r2max_f * (1.0f + 9.5367432e-7f), a.r2max)) {
             const double px = fx, py = fy, pz = fz;
-            const double r2 = __fma_rn(pz, pz, __fma_rn(py, py, __dmul_rn(px, px)));
-            if (r2 > 0.0 && r2 <= a.r2max) {
+            {
                 const double wx = xform_row(a.T + 0, px, py, pz);
                 const double wy = xform_row(a.T + 4, px, py, pz);
                 const double wzd = xform_row(a.T + 8, px, py, pz);

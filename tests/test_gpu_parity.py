@@ -239,3 +239,24 @@ def test_extract_from_random_state(gv):
     compare_voxels(gm, om)
     out, ref = compare_products(gm, om)
     assert np.isfinite(ref["slope"]).sum() > 100
+
+
+def test_points_at_the_range_limit(gv):
+    # points on, just inside and just outside max_range, in many directions:
+    # the device decides the range filter like the oracle's FP64 test
+    rng = np.random.default_rng(31)
+    params = oracle.OracleParams(nx=40, ny=40, nz=24, res=0.25, max_range=3.0)
+    d = rng.normal(size=(3000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    base = (d * 3.0).astype(np.float32)
+    pts = np.concatenate([base, np.nextafter(base, np.float32(0)), np.nextafter(base, np.float32(10)),
+                          np.float32([[3, 0, 0], [0, -3, 0], [0, 0, 3], [3.0000002, 0, 0], [2.9999998, 0, 0]])])
+    T = np.array([[1.0, 0, 0, 0.1], [0, 1.0, 0, -0.05], [0, 0, 1.0, 0.3]])
+    om = oracle.OracleMap(params, (-20, -20, -12))
+    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm.shift((-20, -20, -12))
+    om.ingest(pts, T)
+    gm.ingest(to_dev(pts), T)
+    compare_voxels(gm, om)
+    compare_stats(gm, om)
+    assert 0 < om.stats.rays_valid < len(pts)
