@@ -81,6 +81,8 @@ def _load():
             lib.or_slope.argtypes = [P(OrParams), f32p, f32p, f32p]
             lib.or_negative.argtypes = [P(OrParams), f32p, u8p]
             lib.or_extract.argtypes = [P(OrParams), u32p, u32p, f32p, f32p, f32p, u8p, f32p, f32p]
+            lib.or_lut.argtypes = [P(OrParams), u32p, u32p, f32p, i64p, u32p, u32p, f32p, ctypes.c_int64]
+            lib.or_lut.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -205,6 +207,25 @@ def extract(params: OracleParams, hits, passes, minz) -> dict:
                    _ptr(out["density"], ctypes.c_float), _ptr(out["flags"], ctypes.c_uint8),
                    _ptr(out["slope"], ctypes.c_float), _ptr(out["roughness"], ctypes.c_float))
     return out
+
+
+def lut(params: OracleParams, hits, passes, minz):
+    """Lookup-table encoding (Sec. III-A): (lut int64 (nx,ny,nz), data dict of
+    occupied-voxel arrays in linear order)."""
+    lib = _load()
+    pc = params.c()
+    h = np.ascontiguousarray(hits, dtype=np.uint32)
+    ps = np.ascontiguousarray(passes, dtype=np.uint32)
+    m = np.ascontiguousarray(minz, dtype=np.float32)
+    table = np.zeros(h.shape, dtype=np.int64)
+    cap = int(np.count_nonzero(h))
+    dh = np.zeros(max(cap, 1), np.uint32)
+    dp = np.zeros(max(cap, 1), np.uint32)
+    dm = np.zeros(max(cap, 1), np.float32)
+    n = lib.or_lut(ctypes.byref(pc), _ptr(h, ctypes.c_uint32), _ptr(ps, ctypes.c_uint32), _ptr(m, ctypes.c_float),
+                   _ptr(table, ctypes.c_int64), _ptr(dh, ctypes.c_uint32), _ptr(dp, ctypes.c_uint32),
+                   _ptr(dm, ctypes.c_float), cap)
+    return table, {"hits": dh[:n], "passes": dp[:n], "minz": dm[:n]}
 
 
 def slope_roughness(params: OracleParams, height: np.ndarray):

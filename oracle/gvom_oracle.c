@@ -541,3 +541,33 @@ void or_extract(const or_params* p, const uint32_t* hits, const uint32_t* passes
     or_slope(p, height, slope, rough);
     or_negative(p, height, flags);
 }
+
+/* Lookup-table encoding of the map (Sec. III-A): the data array holds the
+ * metrics (hits, misses, lowest return) of the occupied voxels, in the
+ * order of their logical linear index; the lookup table, one entry per
+ * voxel, holds an occupied voxel's index in the data array and
+ * -1 - N_m (N_m = the voxel's misses) for every other voxel. Entries are
+ * int64 so that -1 - N_m is exact for any 32-bit miss count. Data entries
+ * at or beyond `cap` are not written. Returns the number of occupied
+ * voxels. Pinned by tests: decoding the table gives the state back, the
+ * indices rise with the linear index, and a hand-built grid. */
+int64_t or_lut(const or_params* p, const uint32_t* hits, const uint32_t* passes, const float* minz, int64_t* lut,
+               uint32_t* d_hits, uint32_t* d_passes, float* d_minz, int64_t cap)
+{
+    const int64_t V = (int64_t)p->nx * p->ny * p->nz;
+    int64_t k = 0;
+    for (int64_t i = 0; i < V; ++i) {
+        if (hits[i] >= 1) {
+            lut[i] = k;
+            if (k < cap) {
+                d_hits[k] = hits[i];
+                d_passes[k] = passes[i];
+                d_minz[k] = minz[i];
+            }
+            k += 1;
+        } else {
+            lut[i] = -1 - (int64_t)passes[i];
+        }
+    }
+    return k;
+}

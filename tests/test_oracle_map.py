@@ -266,3 +266,37 @@ def test_sensor_outside_window_counts_only_inside_cells():
     hits, passes, minz, _ = brute_update(params, origin, pts, T)
     np.testing.assert_array_equal(m.passes, passes)
     np.testing.assert_array_equal(m.hits, hits)
+
+
+def test_lut_encoding_hand_built_and_round_trip():
+    # Sec. III-A: occupied voxels index the data array in linear order;
+    # other voxels hold -1 - misses
+    params = oracle.OracleParams(nx=2, ny=2, nz=3, res=0.2)
+    hits = np.zeros((2, 2, 3), np.uint32)
+    passes = np.zeros((2, 2, 3), np.uint32)
+    minz = np.full((2, 2, 3), np.inf, np.float32)
+    hits[0, 0, 2], passes[0, 0, 2], minz[0, 0, 2] = 2, 5, 0.5
+    hits[1, 0, 0], passes[1, 0, 0], minz[1, 0, 0] = 1, 0, -0.25
+    passes[0, 1, 1] = 7
+    passes[1, 1, 2] = 4294967295  # the largest miss count stays exact
+    table, data = oracle.lut(params, hits, passes, minz)
+    expect = np.array([[[-1, -1, 0], [-1, -8, -1]], [[1, -1, -1], [-1, -1, -1 - 4294967295]]], np.int64)
+    np.testing.assert_array_equal(table, expect)
+    np.testing.assert_array_equal(data["hits"], [2, 1])
+    np.testing.assert_array_equal(data["passes"], [5, 0])
+    np.testing.assert_array_equal(data["minz"], np.float32([0.5, -0.25]))
+
+
+def test_lut_round_trip_random_state():
+    rng = np.random.default_rng(12)
+    params = oracle.OracleParams(nx=9, ny=7, nz=5, res=0.2)
+    m = _filled(params, (0, 0, 0), 3)
+    table, data = oracle.lut(params, m.hits, m.passes, m.minz)
+    occ = table >= 0
+    assert np.array_equal(occ, m.hits > 0)
+    idx = table[occ]
+    assert np.array_equal(idx, np.arange(len(idx)))  # rising with the linear index
+    np.testing.assert_array_equal(data["hits"][idx], m.hits[occ])
+    np.testing.assert_array_equal(data["passes"][idx], m.passes[occ])
+    np.testing.assert_array_equal(data["minz"][idx], m.minz[occ])
+    np.testing.assert_array_equal(-1 - table[~occ], m.passes[~occ].astype(np.int64))
