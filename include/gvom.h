@@ -226,6 +226,33 @@ GVOM_API int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t* h
 GVOM_API int gvom_extract_voxels(struct gvom_map* map, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
                         gvom_stream_t stream);
 
+/* Folds k scans from different sensors into the map in one per-point pass
+ * and one traversal launch (Sec. III: several pointclouds feed one map).
+ * Scan j has n[j] points at pts_dev[j] (device, same stride for all, as
+ * gvom_ingest_scan) and its own sensor-to-world pose T_ws + 12*j. The
+ * window does not move (shift first with gvom_shift). The result equals
+ * k calls of gvom_ingest_scan, in any order: counts add and the lowest
+ * return is a minimum. 1 <= k <= GVOM_MAX_MULTI_SCANS; the points of all
+ * scans together must not exceed GVOM_MAX_SCAN_POINTS. Invalid arguments
+ * change nothing. The map keeps the tables this needs between calls and
+ * may synchronise the stream when they grow. Stream-ordered. */
+#define GVOM_MAX_MULTI_SCANS 4096
+GVOM_API int gvom_ingest_multi(struct gvom_map* map, int32_t k, const float* const* pts_dev, const int64_t* n,
+                               int32_t stride, const double* T_ws, gvom_stream_t stream);
+
+/* Exports the map in the paper's storage format (Sec. III-A): a lookup
+ * table with one int64 entry per voxel, in logical (window) order, holding
+ * the voxel's index in the data array if it is occupied (hits >= 1) and
+ * -1 - N_m otherwise (N_m = its misses, i.e. pass count); and the data
+ * array of the occupied voxels' hits, misses and lowest return, in the
+ * same linear order. The number of occupied voxels is written to
+ * *n_occupied_dev (device int64); data entries at or beyond data_capacity
+ * are not written (call again with larger buffers if *n_occupied_dev
+ * exceeds it). Deterministic. Stream-ordered. */
+GVOM_API int gvom_export_lut(struct gvom_map* map, int64_t* lut_dev, uint32_t* data_hits_dev,
+                             uint32_t* data_passes_dev, float* data_minz_dev, int64_t data_capacity,
+                             int64_t* n_occupied_dev, gvom_stream_t stream);
+
 /* Reads the counters. Synchronises with the map's last enqueued work
  * (device-wide synchronisation). Returns GVOM_ERR_TIMEOUT (with *out still
  * filled) if, since creation or the last gvom_reset_stats, a bounded wait

@@ -120,6 +120,8 @@ def load_library():
             "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
             "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
+            "gvom_ingest_multi": ([vp, i32, P(vp), P(i64), i32, P(ctypes.c_double), vp], ctypes.c_int),
+            "gvom_export_lut": ([vp, vp, vp, vp, vp, i64, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -270,6 +272,33 @@ def gvom_extract_maps_noalloc(cfg: gvom_config, hits, passes, minz, height=None,
     _check(load_library().gvom_extract_maps_noalloc(ctypes.byref(cfg), hits.data_ptr(), passes.data_ptr(),
                                                     minz.data_ptr(), ctypes.byref(out), _stream_handle(stream)),
            "gvom_extract_maps_noalloc")
+
+
+def gvom_ingest_multi(handle: int, points, T_ws, stream=None) -> None:
+    """points: list of k device float32 (n_j, 3|4) tensors; T_ws: k poses."""
+    import numpy as np
+    k = len(points)
+    if k != len(T_ws) or k < 1:
+        raise ValueError("one pose per scan, at least one scan")
+    strides = {int(p.shape[1]) for p in points}
+    if len(strides) != 1:
+        raise ValueError("all scans must have the same stride")
+    for p in points:
+        if p.dtype.is_floating_point is False or p.element_size() != 4 or not p.is_contiguous():
+            raise ValueError("points must be contiguous float32")
+    ptrs = (ctypes.c_void_p * k)(*[p.data_ptr() if p.shape[0] else None for p in points])
+    ns = (ctypes.c_int64 * k)(*[int(p.shape[0]) for p in points])
+    T = np.ascontiguousarray(np.stack([np.asarray(t, dtype=np.float64).reshape(12) for t in T_ws]))
+    Tc = (ctypes.c_double * (12 * k))(*T.reshape(-1).tolist())
+    _check(load_library().gvom_ingest_multi(handle, k, ptrs, ns, strides.pop(), Tc, _stream_handle(stream)),
+           "gvom_ingest_multi")
+
+
+def gvom_export_lut(handle: int, lut, data_hits, data_passes, data_minz, data_capacity: int, n_occupied,
+                    stream=None) -> None:
+    ptrs = [t.data_ptr() if t is not None else None for t in (lut, data_hits, data_passes, data_minz)]
+    _check(load_library().gvom_export_lut(handle, *ptrs, int(data_capacity), n_occupied.data_ptr(),
+                                          _stream_handle(stream)), "gvom_export_lut")
 
 
 def gvom_extract_voxels(handle: int, hits=None, passes=None, minz=None, stream=None) -> None:
@@ -448,6 +477,27 @@ class VoxelMap:
         minz = torch.empty(shp, dtype=torch.float32, device="cuda")
         gvom_extract_voxels(self.handle, hits, passes, minz, stream)
         return hits, passes, minz
+
+    def ingest_multi(self, points, T_ws, stream=None):
+        gvom_ingest_multi(self.handle, points, T_ws, stream)
+
+    def export_lut(self, capacity=None, stream=None):
+        """The lookup table (int64, window shape) and the occupied voxels'
+        data (hits, passes, minz) in the paper's storage format. With no
+        capacity given, the data arrays are sized from a first counting call."""
+        import torch
+        lut = torch.empty(self.shape, dtype=torch.int64, device="cuda")
+        n_occ = torch.zeros(1, dtype=torch.int64, device="cuda")
+        if capacity is None:
+            gvom_export_lut(self.handle, lut, None, None, None, 0, n_occ, stream)
+            torch.cuda.synchronize()
+            capacity = int(n_occ.item())
+        dh = torch.empty(capacity, dtype=torch.int32, device="cuda")
+        dp = torch.empty(capacity, dtype=torch.int32, device="cuda")
+        dm = torch.empty(capacity, dtype=torch.float32, device="cuda")
+        gvom_export_lut(self.handle, lut, dh if capacity else None, dp if capacity else None,
+                        dm if capacity else None, capacity, n_occ, stream)
+        return lut, n_occ, {"hits": dh, "passes": dp, "minz": dm}
 
     def stats(self):
         return gvom_get_stats(self.handle)

@@ -214,6 +214,7 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
     if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&m->lut_counts, sizeof(unsigned int) * (size_t)gvom::lut_blocks(V));
     if (e == cudaSuccess) e = cudaMemset(m->s.counters, 0, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = gvom::launch_init_state(m->s, V, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -237,6 +238,8 @@ void gvom_destroy(gvom_map* m) {
     cudaFree(m->w.rays);
     cudaFree(m->w.items);
     cudaFree(m->w.item_count);
+    cudaFree(m->lut_counts);
+    if (m->multi) gvom_batch_destroy(m->multi);
     delete m;
 }
 
@@ -355,6 +358,30 @@ int gvom_extract_voxels(gvom_map* m, uint32_t* hits_dev, uint32_t* passes_dev, f
     if (!hits_dev && !passes_dev && !minz_dev) return GVOM_OK;
     return cuda_status(
         gvom::launch_gather_voxels(m->s, geom_of(m), hits_dev, passes_dev, minz_dev, (cudaStream_t)stream));
+}
+
+int gvom_ingest_multi(gvom_map* m, int32_t k, const float* const* pts_dev, const int64_t* n, int32_t stride,
+                      const double* T_ws, gvom_stream_t stream) {
+    if (!m || !pts_dev || !n || !T_ws || k < 1 || k > GVOM_MAX_MULTI_SCANS || (stride != 3 && stride != 4))
+        return GVOM_ERR_INVALID_ARG;
+    long long total = 0;
+    for (int j = 0; j < k; ++j) {
+        if (n[j] < 0 || n[j] > GVOM_MAX_SCAN_POINTS || (n[j] > 0 && !pts_dev[j])) return GVOM_ERR_INVALID_ARG;
+        if ((((uintptr_t)pts_dev[j]) & (stride == 4 ? 15u : 3u)) != 0) return GVOM_ERR_INVALID_ARG;
+        if (!valid_pose(T_ws + 12 * j)) return GVOM_ERR_INVALID_ARG;
+        total += n[j];
+    }
+    if (total > GVOM_MAX_SCAN_POINTS) return GVOM_ERR_INVALID_ARG;
+    return gvom::ingest_multi(m, k, pts_dev, n, stride, T_ws, (cudaStream_t)stream);
+}
+
+int gvom_export_lut(gvom_map* m, int64_t* lut_dev, uint32_t* data_hits_dev, uint32_t* data_passes_dev,
+                    float* data_minz_dev, int64_t data_capacity, int64_t* n_occupied_dev, gvom_stream_t stream) {
+    if (!m || !lut_dev || !n_occupied_dev || data_capacity < 0) return GVOM_ERR_INVALID_ARG;
+    if (data_capacity > 0 && (!data_hits_dev || !data_passes_dev || !data_minz_dev)) return GVOM_ERR_INVALID_ARG;
+    return cuda_status(gvom::launch_export_lut(m->s, geom_of(m), m->lut_counts, (long long*)n_occupied_dev,
+                                               (long long*)lut_dev, data_hits_dev, data_passes_dev, data_minz_dev,
+                                               data_capacity, (cudaStream_t)stream));
 }
 
 int gvom_get_stats(gvom_map* m, gvom_stats* out) {

@@ -116,6 +116,44 @@ void drop_graph(gvom_batch* b) {
     b->exec = nullptr;
 }
 
+// Grows the segment work list to hold `items` entries (synchronising first).
+int grow_items(gvom_batch* b, long long items, cudaStream_t st) {
+    if (items <= b->w.cap_items) return GVOM_OK;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return gvom::cuda_status(e);
+    cudaFree(b->w.items);
+    b->w.items = nullptr;
+    b->w.cap_items = 0;
+    const long long cap = items + items / 4;
+    e = cudaMalloc(&b->w.items, sizeof(uint2) * (size_t)cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return GVOM_ERR_OUT_OF_MEMORY;
+    }
+    b->w.cap_items = cap;
+    drop_graph(b);
+    return GVOM_OK;
+}
+
+IngestArgs ingest_args(const gvom_map* mp, const float* pts, long long n, int stride, int seg_len, const double* T,
+                       const gvom::RayScratch& w) {
+    IngestArgs a;
+    memset(&a, 0, sizeof(a));
+    a.pts = pts;
+    a.n = n;
+    a.stride = stride;
+    a.seg_len = seg_len;
+    for (int k = 0; k < 12; ++k) a.T[k] = T[k];
+    a.S = 256.0 * (1.0 / mp->cfg.res);
+    a.r2max = mp->cfg.max_range * mp->cfg.max_range;
+    for (int k = 0; k < 3; ++k) a.neg_o256[k] = -256.0 * (double)mp->origin[k];
+    a.g = gvom::geom_of(mp);
+    a.s = mp->s;
+    a.w = w;
+    return a;
+}
+
 }  // namespace
 
 extern "C" {
@@ -212,22 +250,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     }
 
     // the segment work list for this step's points
-    if (items > b->w.cap_items) {
-        cudaError_t e = cudaStreamSynchronize(st);
-        if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return gvom::cuda_status(e);
-        cudaFree(b->w.items);
-        b->w.items = nullptr;
-        b->w.cap_items = 0;
-        long long cap = items + items / 4;
-        e = cudaMalloc(&b->w.items, sizeof(uint2) * (size_t)cap);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return GVOM_ERR_OUT_OF_MEMORY;
-        }
-        b->w.cap_items = cap;
-        drop_graph(b);
-    }
+    const int grown = grow_items(b, items, st);
+    if (grown != GVOM_OK) return grown;
 
     // fill this step's tables in the pinned buffer not in flight
     const int cur = b->cur;
@@ -259,19 +283,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         h.shift_prefix[m] = shift_total;
         shift_total += gvom::shift_units(g, d, whole);
 
-        IngestArgs& a = h.ing[m];
-        memset(&a, 0, sizeof(a));
-        a.pts = pts_dev[m];
-        a.n = n[m];
-        a.stride = stride;
-        a.seg_len = b->tune.seg_len;
-        for (int k = 0; k < 12; ++k) a.T[k] = T_ws[12 * m + k];
-        a.S = 256.0 * (1.0 / mp->cfg.res);
-        a.r2max = mp->cfg.max_range * mp->cfg.max_range;
-        for (int k = 0; k < 3; ++k) a.neg_o256[k] = -256.0 * (double)mp->origin[k];
-        a.g = g;
-        a.s = mp->s;
-        a.w = b->w;
+        h.ing[m] = ingest_args(mp, pts_dev[m], n[m], stride, b->tune.seg_len, T_ws + 12 * m, b->w);
         h.ray_prefix[m] = ray_blocks;
         ray_blocks += (n[m] + 255) / 256;
         h.ray_base[m] = ray_base;
@@ -354,3 +366,82 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
 }
 
 }  // extern "C"
+
+namespace gvom {
+
+// Several scans (one per sensor, each with its own pose) folded into one
+// map with one per-point pass and one segment walk: the batch tables hold
+// one entry per scan, all on the same map and with no shift. The map's
+// batch (created here on first use, re-created when a call needs more
+// entries or points) runs without a graph.
+int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t* n, int stride, const double* T_ws,
+                 cudaStream_t st) {
+    long long total = 0;
+    for (int j = 0; j < k; ++j) total += n[j];
+    gvom_batch* b = mp->multi;
+    if (!b || b->max_maps < k || b->max_points < total) {
+        const int maps = b && b->max_maps > k ? b->max_maps : (k > 8 ? k : 8);
+        long long pts = b && b->max_points > total ? b->max_points : total + total / 4;
+        if (pts < 1) pts = 1;
+        if (pts > GVOM_MAX_SCAN_POINTS) pts = GVOM_MAX_SCAN_POINTS;
+        if (b) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_status(e);
+            gvom_batch_destroy(b);
+            mp->multi = nullptr;
+        }
+        const int rc = gvom_batch_create(maps, pts, 0, &mp->multi);
+        if (rc != GVOM_OK) return rc;
+        b = mp->multi;
+    }
+    const Geom g = geom_of(mp);
+    const int rc = grow_items(b, total * max_segments_per_ray(g, mp->tune.seg_len), st);
+    if (rc != GVOM_OK) return rc;
+
+    const int cur = b->cur;
+    cudaError_t e = cudaEventSynchronize(b->copied[cur]);
+    if (e != cudaSuccess) return cuda_status(e);
+    BatchTables h = tables_at(b->h_tables[cur], b->L);
+    long long ray_blocks = 0, ray_base = 0;
+    for (int j = 0; j < k; ++j) {
+        BatchShift& sh = h.sh[j];
+        memset(&sh, 0, sizeof(sh));
+        sh.s = mp->s;
+        sh.g = g;
+        h.shift_prefix[j] = 0;
+        h.ing[j] = ingest_args(mp, pts_dev[j], n[j], stride, mp->tune.seg_len, T_ws + 12 * j, b->w);
+        h.ray_prefix[j] = ray_blocks;
+        ray_blocks += (n[j] + 255) / 256;
+        h.ray_base[j] = ray_base;
+        ray_base += n[j];
+        h.col_prefix[j] = 0;
+        h.tile_prefix[j] = 0;
+    }
+    h.shift_prefix[k] = 0;
+    h.ray_prefix[k] = ray_blocks;
+    h.col_prefix[k] = 0;
+    h.tile_prefix[k] = 0;
+    h.hdr->B = k;
+    h.hdr->shift_total = 0;
+    h.hdr->ray_blocks = ray_blocks;
+    h.hdr->col_tasks = 0;
+    h.hdr->tiles = 0;
+    mp->scans += k;
+    mp->points_in += total;
+
+    e = cudaMemcpyAsync(b->d_tables, b->h_tables[cur], b->L.bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->copied[cur], st);
+    if (e != cudaSuccess) return cuda_status(e);
+    b->cur ^= 1;
+
+    IngestArgs shared;
+    memset(&shared, 0, sizeof(shared));
+    shared.w = b->w;
+    MarchShape shape;
+    shape.block = mp->tune.march_block;
+    shape.blocks_per_sm = mp->tune.march_blocks_per_sm;
+    const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
+    return cuda_status(launch_batch_update(tables_at(b->d_tables, b->L), b->max_maps, max_ray_blocks, shared, shape, st));
+}
+
+}  // namespace gvom

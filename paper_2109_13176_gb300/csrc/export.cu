@@ -1,0 +1,164 @@
+// Export of a map in the paper's storage format (G-VOM Sec. III-A): a
+// lookup table over the window and a data array of the occupied voxels.
+//
+// The table holds, for each voxel in logical linear order, the voxel's index
+// in the data array if it is occupied (hits >= 1) and -1 - N_m otherwise
+// (N_m = its misses, the pass count); the data array holds the occupied
+// voxels' hits, misses and lowest return in that same order. The order is
+// deterministic: three kernels count occupied voxels per 1024-voxel block,
+// scan the block counts, then write each block's voxels at their global
+// ranks.
+#include "gvom_internal.h"
+
+namespace gvom {
+
+namespace {
+
+constexpr int kLutBlock = 256;
+constexpr int kLutPer = 4;                      // consecutive voxels per thread
+constexpr int kLutSpan = kLutBlock * kLutPer;   // voxels per block
+
+__device__ __forceinline__ uint32_t logical_to_phys(const Geom& g, long long i) {
+    const uint32_t cz = (uint32_t)i % (uint32_t)g.nz;  // i < V < 2^31
+    const uint32_t col = (uint32_t)i / (uint32_t)g.nz;
+    const uint32_t cy = col % (uint32_t)g.ny, cx = col / (uint32_t)g.ny;
+    int px = (int)cx + g.rx;
+    px -= (px >= g.nx) ? g.nx : 0;
+    int py = (int)cy + g.ry;
+    py -= (py >= g.ny) ? g.ny : 0;
+    int pz = (int)cz + g.rz;
+    pz -= (pz >= g.nz) ? g.nz : 0;
+    return ((uint32_t)px * g.ny + py) * (uint32_t)g.nz + pz;
+}
+
+// Exclusive block-wide scan of one value per thread (kLutBlock threads).
+__device__ __forceinline__ unsigned int block_exclusive(unsigned int v, unsigned int* warp_sums, unsigned int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int s = 0;
+        for (int w = 0; w < kLutBlock / 32; ++w) {
+            const unsigned int t = warp_sums[w];
+            warp_sums[w] = s;
+            s += t;
+        }
+        *total = s;
+    }
+    __syncthreads();
+    return warp_sums[warp] + x - v;
+}
+
+__global__ void __launch_bounds__(kLutBlock) k_lut_count(MapState s, Geom g, long long V, unsigned int* counts) {
+    __shared__ unsigned int warp_sums[kLutBlock / 32];
+    __shared__ unsigned int total;
+    const long long i0 = (long long)blockIdx.x * kLutSpan + (long long)threadIdx.x * kLutPer;
+    unsigned int c = 0;
+#pragma unroll
+    for (int k = 0; k < kLutPer; ++k)
+        if (i0 + k < V) c += s.hits[logical_to_phys(g, i0 + k)] != 0u ? 1u : 0u;
+    block_exclusive(c, warp_sums, &total);
+    if (threadIdx.x == 0) counts[blockIdx.x] = total;
+}
+
+// One block scans all block counts in place (exclusive) and writes the total.
+__global__ void __launch_bounds__(1024) k_lut_scan(unsigned int* counts, long long nblocks, long long* n_occupied) {
+    __shared__ unsigned long long warp_sums[32];
+    __shared__ unsigned long long carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nblocks; base += 1024) {
+        const long long i = base + threadIdx.x;
+        const unsigned long long v = i < nblocks ? counts[i] : 0ull;
+        unsigned long long x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long sum = 0;
+            for (int w = 0; w < 32; ++w) {
+                const unsigned long long t = warp_sums[w];
+                warp_sums[w] = sum;
+                sum += t;
+            }
+        }
+        __syncthreads();
+        const unsigned long long excl = carry + warp_sums[warp] + x - v;
+        if (i < nblocks) counts[i] = (unsigned int)excl;  // prefixes fit 32 bits: V < 2^31
+        __syncthreads();                                  // every thread has read carry
+        if (threadIdx.x == 1023) carry = excl + v;        // the tile's end
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_occupied = (long long)carry;
+}
+
+__global__ void __launch_bounds__(kLutBlock)
+    k_lut_write(MapState s, Geom g, long long V, const unsigned int* prefix, long long* lut, uint32_t* d_hits,
+                uint32_t* d_passes, float* d_minz, long long cap) {
+    __shared__ unsigned int warp_sums[kLutBlock / 32];
+    __shared__ unsigned int total;
+    const long long i0 = (long long)blockIdx.x * kLutSpan + (long long)threadIdx.x * kLutPer;
+    uint32_t k_[kLutPer];
+    uint32_t h_[kLutPer];
+    unsigned int c = 0;
+#pragma unroll
+    for (int k = 0; k < kLutPer; ++k) {
+        k_[k] = 0;
+        h_[k] = 0;
+        if (i0 + k < V) {
+            k_[k] = logical_to_phys(g, i0 + k);
+            h_[k] = s.hits[k_[k]];
+            c += h_[k] != 0u ? 1u : 0u;
+        }
+    }
+    long long idx = (long long)prefix[blockIdx.x] + block_exclusive(c, warp_sums, &total);
+#pragma unroll
+    for (int k = 0; k < kLutPer; ++k) {
+        if (i0 + k >= V) break;
+        const uint32_t pm = s.passes[k_[k]];
+        if (h_[k] != 0u) {
+            lut[i0 + k] = idx;
+            if (idx < cap) {
+                d_hits[idx] = h_[k];
+                d_passes[idx] = pm;
+                d_minz[idx] = s.minz[k_[k]];
+            }
+            idx += 1;
+        } else {
+            lut[i0 + k] = -1 - (long long)pm;
+        }
+    }
+}
+
+}  // namespace
+
+long long lut_blocks(long long V) { return (V + kLutSpan - 1) / kLutSpan; }
+
+cudaError_t launch_export_lut(const MapState& s, const Geom& g, unsigned int* counts, long long* n_occupied,
+                              long long* lut, uint32_t* dh, uint32_t* dp, float* dm, long long cap, cudaStream_t st) {
+    const long long V = (long long)g.nx * g.ny * g.nz;
+    const long long nb = lut_blocks(V);
+    count_launch();
+    k_lut_count<<<(unsigned)nb, kLutBlock, 0, st>>>(s, g, V, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    count_launch();
+    k_lut_scan<<<1, 1024, 0, st>>>(counts, nb, n_occupied);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    count_launch();
+    k_lut_write<<<(unsigned)nb, kLutBlock, 0, st>>>(s, g, V, counts, lut, dh, dp, dm, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace gvom

@@ -126,6 +126,12 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
                                 const MarchShape& shape, cudaStream_t st);
 cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st);
 
+// Lookup-table export (export.cu): blocks of the count / write kernels and
+// the three launches (count, scan, write).
+long long lut_blocks(long long V);
+cudaError_t launch_export_lut(const MapState& s, const Geom& g, unsigned int* counts, long long* n_occupied,
+                              long long* lut, uint32_t* dh, uint32_t* dp, float* dm, long long cap, cudaStream_t st);
+
 // Whether a configuration is within the documented limits (include/gvom.h).
 bool valid_config(const gvom_config* c);
 
@@ -161,6 +167,8 @@ struct gvom_map {
     gvom::MapState s;
     gvom::RayScratch w;     // per-scan ray records and segment work list
     float* height_scratch;  // nx * ny, used when the caller asks for no height
+    unsigned int* lut_counts;  // per-block counts of the lookup-table export
+    struct gvom_batch* multi;  // tables for gvom_ingest_multi (created on first use)
     gvom_tuning tune;
     long long scans;
     long long points_in;
@@ -175,4 +183,7 @@ bool valid_origin(const int64_t o[3]);
 ExtractParams extract_params(const gvom_map* m);
 bool valid_pose(const double T[12]);
 bool valid_tuning(const gvom_tuning* t);
+// gvom_ingest_multi after validation (batch.cu).
+int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t* n, int stride, const double* T_ws,
+                 cudaStream_t st);
 }  // namespace gvom

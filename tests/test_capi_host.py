@@ -69,6 +69,10 @@ def test_null_arguments_rejected(lib):
     assert lib.gvom_get_stats(None, None) == gv.GVOM_ERR_INVALID_ARG
     assert lib.gvom_origin_for_pose(None, None, o) == gv.GVOM_ERR_INVALID_ARG
     assert lib.gvom_config_default(None) == gv.GVOM_ERR_INVALID_ARG
+    ptrs = (ctypes.c_void_p * 1)()
+    ns = (ctypes.c_int64 * 1)(0)
+    assert lib.gvom_ingest_multi(None, 1, ptrs, ns, 3, T, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_export_lut(None, None, None, None, None, 0, None, None) == gv.GVOM_ERR_INVALID_ARG
     lib.gvom_destroy(None)  # no-op
 
 
