@@ -192,6 +192,69 @@ class OracleMap:
         return extract(p, self.hits, self.passes, self.minz)
 
 
+class BufferedOracleMap:
+    """The map buffer of Sec. III-A/III-B: the last K per-scan maps. Each
+    per-scan map is one scan folded into an empty map at the window of its
+    moment, and moves with every later window shift (voxels that leave are
+    lost, voxels that enter are empty). The map the products come from
+    combines the buffer: hits and passes summed (mod 2^32, like the uint32
+    counts), lowest return the minimum."""
+
+    def __init__(self, params: OracleParams, K: int, origin=(0, 0, 0)):
+        if K < 1:
+            raise ValueError("K >= 1")
+        self.params = params
+        self.K = K
+        self.origin = np.array(origin, dtype=np.int64)
+        self.scans: list[OracleMap] = []
+        self.stats = OrStats()
+
+    def shift_to(self, new_origin) -> None:
+        for m in self.scans:
+            m.shift_to(new_origin)
+        self.origin = np.array(new_origin, dtype=np.int64)
+
+    def shift_for_pose(self, vehicle_xyz) -> None:
+        self.shift_to(origin_for_pose(self.params, vehicle_xyz))
+
+    def ingest(self, points: np.ndarray, T_ws: np.ndarray) -> OrStats:
+        m = OracleMap(self.params, self.origin)
+        st = m.ingest(points, T_ws)
+        self.scans.append(m)
+        if len(self.scans) > self.K:
+            self.scans.pop(0)
+        for f, _ in OrStats._fields_:
+            setattr(self.stats, f, getattr(self.stats, f) + getattr(st, f))
+        return st
+
+    def _combine(self):
+        p = self.params
+        shape = (p.nx, p.ny, p.nz)
+        h = np.zeros(shape, dtype=np.uint64)
+        ps = np.zeros(shape, dtype=np.uint64)
+        mz = np.full(shape, np.inf, dtype=np.float32)
+        for m in self.scans:
+            h += m.hits
+            ps += m.passes
+            mz = np.minimum(mz, m.minz)
+        return h.astype(np.uint32), ps.astype(np.uint32), mz
+
+    @property
+    def hits(self):
+        return self._combine()[0]
+
+    @property
+    def passes(self):
+        return self._combine()[1]
+
+    @property
+    def minz(self):
+        return self._combine()[2]
+
+    def extract(self) -> dict:
+        return extract(self.params, *self._combine())
+
+
 def extract(params: OracleParams, hits, passes, minz) -> dict:
     """All 2D products: height, density, flags, slope, roughness, shape (nx, ny)."""
     lib = _load()
