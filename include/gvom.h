@@ -66,10 +66,25 @@ typedef enum gvom_status {
  * Limits: 1 <= nx, ny, nz <= 4096 with nx * ny * nz < 2^31; res > 0;
  * 0 < max_range with max_range / res <= 8192; 0 <= obs_min_h <= obs_max_h;
  * 0 < hard_den <= 65535, hard_num <= hard_den; slope_n odd in [3, 15];
- * 3 <= slope_min_px <= slope_n^2; 1 <= neg_max_px <= 64. */
+ * 3 <= slope_min_px <= slope_n^2; 1 <= neg_max_px <= 64;
+ * 0 <= scan_buffer <= GVOM_MAX_SCAN_BUFFER.
+ *
+ * Scan buffer (Sec. III-A, III-B: per-scan maps kept in a buffer and
+ * combined). With scan_buffer = K > 0 the map also keeps each of its last K
+ * scans' own counts and lowest returns (K more copies of the voxel state,
+ * 12 bytes per voxel each), moved with the window like the map. Every scan
+ * (an empty one too; each scan of gvom_ingest_multi, which then takes at
+ * most K) takes the slot of the oldest, whose counts are first taken out of
+ * the map (exact: counts subtract) and whose lowest returns are recomputed
+ * from the slots that stay. The map thus always equals the combination of
+ * its last K scans: counts summed, lowest return the minimum. gvom_reset
+ * empties the buffer. K = 0: every scan accumulates (an unbounded buffer). */
+#define GVOM_MAX_SCAN_BUFFER 64
 typedef struct gvom_config {
     int32_t nx, ny, nz;   /* window size in voxels */
-    int32_t reserved0;    /* must be 0 */
+    int32_t scan_buffer;  /* 0: the map accumulates every scan; K in [1, 64]:
+                             the map is the combination of its last K scans
+                             (Sec. III-A map buffer; see below) */
     double res;           /* voxel edge, metres */
     double max_range;     /* returns beyond this range are dropped, metres */
     float obs_min_h;      /* positive obstacle band above ground, metres */

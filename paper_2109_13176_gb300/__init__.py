@@ -38,7 +38,7 @@ class GvomError(RuntimeError):
 class gvom_config(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("scan_buffer", ctypes.c_int32),
         ("res", ctypes.c_double), ("max_range", ctypes.c_double),
         ("obs_min_h", ctypes.c_float), ("obs_max_h", ctypes.c_float),
         ("hard_num", ctypes.c_uint32), ("hard_den", ctypes.c_uint32),

@@ -29,7 +29,7 @@ bool valid_config(const gvom_config* c) {
     if (!c) return false;
     if (c->nx < 1 || c->ny < 1 || c->nz < 1 || c->nx > 4096 || c->ny > 4096 || c->nz > 4096) return false;
     if ((long long)c->nx * c->ny * c->nz >= (1LL << 31)) return false;
-    if (c->reserved0 != 0) return false;
+    if (c->scan_buffer < 0 || c->scan_buffer > GVOM_MAX_SCAN_BUFFER) return false;
     if (!(c->res > 0.0) || !isfinite(c->res)) return false;
     if (!(c->max_range > 0.0) || !isfinite(c->max_range) || !(c->max_range / c->res <= 8192.0)) return false;
     if (!(c->obs_min_h >= 0.0f) || !(c->obs_max_h >= c->obs_min_h) || !isfinite(c->obs_max_h)) return false;
@@ -215,6 +215,14 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
     if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&m->lut_counts, sizeof(unsigned int) * (size_t)gvom::lut_blocks(V));
+    m->s.V = (uint32_t)V;
+    const int K = cfg->scan_buffer;
+    if (K > 0) {
+        if (e == cudaSuccess) e = cudaMalloc(&m->s.ring_hits, sizeof(uint32_t) * (size_t)V * K);
+        if (e == cudaSuccess) e = cudaMalloc(&m->s.ring_passes, sizeof(uint32_t) * (size_t)V * K);
+        if (e == cudaSuccess) e = cudaMalloc(&m->s.ring_minz, sizeof(float) * (size_t)V * K);
+        if (e == cudaSuccess) m->s.ring_K = K;
+    }
     if (e == cudaSuccess) e = cudaMemset(m->s.counters, 0, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = gvom::launch_init_state(m->s, V, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -239,6 +247,9 @@ void gvom_destroy(gvom_map* m) {
     cudaFree(m->w.items);
     cudaFree(m->w.item_count);
     cudaFree(m->lut_counts);
+    cudaFree(m->s.ring_hits);
+    cudaFree(m->s.ring_passes);
+    cudaFree(m->s.ring_minz);
     if (m->multi) gvom_batch_destroy(m->multi);
     delete m;
 }
@@ -273,6 +284,8 @@ int gvom_get_origin(const gvom_map* m, int64_t out_origin[3]) {
 int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
     if (!m || !origin || !valid_origin(origin)) return GVOM_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k) m->origin[k] = origin[k];
+    m->buf_head = 0;
+    m->buf_occupied = 0;
     return cuda_status(gvom::launch_init_state(m->s, voxels(m), (cudaStream_t)stream));
 }
 
@@ -300,14 +313,20 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     if (stride == 4 && (((uintptr_t)pts_dev) & 15u) != 0) return GVOM_ERR_INVALID_ARG;
     if ((((uintptr_t)pts_dev) & 3u) != 0) return GVOM_ERR_INVALID_ARG;
     if (!valid_pose(T_ws)) return GVOM_ERR_INVALID_ARG;
+    int rc = n > 0 ? ensure_capacity(m, n, (cudaStream_t)stream) : GVOM_OK;
+    if (rc != GVOM_OK) return rc;
+    // with a scan buffer, this scan takes the oldest slot (an empty scan too)
+    int slot = -1;
+    const unsigned long long evict = gvom::take_slots(m, 1, &slot);
+    rc = cuda_status(gvom::launch_evict(m->s, evict, (cudaStream_t)stream));
+    if (rc != GVOM_OK) return rc;
     if (n == 0) {
         m->scans += 1;
         return GVOM_OK;
     }
-    int rc = ensure_capacity(m, n, (cudaStream_t)stream);
-    if (rc != GVOM_OK) return rc;
     IngestArgs a;
     memset(&a, 0, sizeof(a));
+    a.slot = slot;
     a.pts = pts_dev;
     a.n = n;
     a.stride = stride;
@@ -360,10 +379,34 @@ int gvom_extract_voxels(gvom_map* m, uint32_t* hits_dev, uint32_t* passes_dev, f
         gvom::launch_gather_voxels(m->s, geom_of(m), hits_dev, passes_dev, minz_dev, (cudaStream_t)stream));
 }
 
+}  // extern "C"
+
+namespace gvom {
+unsigned long long take_slots(gvom_map* m, int k, int* slots) {
+    const int K = m->cfg.scan_buffer;
+    unsigned long long mask = 0;
+    for (int j = 0; j < k; ++j) {
+        if (K == 0) {
+            slots[j] = -1;
+            continue;
+        }
+        const int sl = m->buf_head;
+        slots[j] = sl;
+        mask |= m->buf_occupied & (1ull << sl);
+        m->buf_occupied |= 1ull << sl;
+        m->buf_head = sl + 1 == K ? 0 : sl + 1;
+    }
+    return mask;
+}
+}  // namespace gvom
+
+extern "C" {
+
 int gvom_ingest_multi(gvom_map* m, int32_t k, const float* const* pts_dev, const int64_t* n, int32_t stride,
                       const double* T_ws, gvom_stream_t stream) {
     if (!m || !pts_dev || !n || !T_ws || k < 1 || k > GVOM_MAX_MULTI_SCANS || (stride != 3 && stride != 4))
         return GVOM_ERR_INVALID_ARG;
+    if (m->cfg.scan_buffer > 0 && k > m->cfg.scan_buffer) return GVOM_ERR_INVALID_ARG;
     long long total = 0;
     for (int j = 0; j < k; ++j) {
         if (n[j] < 0 || n[j] > GVOM_MAX_SCAN_POINTS || (n[j] > 0 && !pts_dev[j])) return GVOM_ERR_INVALID_ARG;

@@ -32,7 +32,8 @@ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 // Byte offsets of the table arrays inside one allocation.
 struct Layout {
-    size_t hdr, ing, sh, ex, shift_prefix, ray_prefix, ray_base, col_prefix, tile_prefix, sensors, bytes;
+    size_t hdr, ing, sh, ex, shift_prefix, ray_prefix, ray_base, col_prefix, tile_prefix, sensors, evict_prefix,
+        bytes;
 };
 
 Layout layout_for(int max_maps) {
@@ -58,6 +59,8 @@ Layout layout_for(int max_maps) {
     o = align16(o + sizeof(long long) * (max_maps + 1));
     L.sensors = o;
     o = align16(o + sizeof(int4) * max_maps);
+    L.evict_prefix = o;
+    o = align16(o + sizeof(long long) * (max_maps + 1));
     L.bytes = o;
     return L;
 }
@@ -74,6 +77,7 @@ BatchTables tables_at(char* base, const Layout& L) {
     t.col_prefix = reinterpret_cast<long long*>(base + L.col_prefix);
     t.tile_prefix = reinterpret_cast<long long*>(base + L.tile_prefix);
     t.sensors = reinterpret_cast<int4*>(base + L.sensors);
+    t.evict_prefix = reinterpret_cast<long long*>(base + L.evict_prefix);
     return t;
 }
 
@@ -93,7 +97,7 @@ struct gvom_batch {
     // captured graph and what it was captured for
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
-    int g_B, g_extract, g_halo;
+    int g_B, g_extract, g_halo, g_slots;
     long long g_cap_items;
     long long g_kernels;  // kernels in the captured graph, counted per replay
     long long steps;
@@ -140,6 +144,7 @@ IngestArgs ingest_args(const gvom_map* mp, const float* pts, long long n, int st
                        const gvom::RayScratch& w) {
     IngestArgs a;
     memset(&a, 0, sizeof(a));
+    a.slot = -1;
     a.pts = pts;
     a.n = n;
     a.stride = stride;
@@ -258,7 +263,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     cudaError_t e = cudaEventSynchronize(b->copied[cur]);
     if (e != cudaSuccess) return gvom::cuda_status(e);
     BatchTables h = tables_at(b->h_tables[cur], b->L);
-    long long shift_total = 0, ray_blocks = 0, col_tasks = 0, tiles = 0, ray_base = 0;
+    long long shift_total = 0, ray_blocks = 0, col_tasks = 0, tiles = 0, ray_base = 0, evict_total = 0;
+    int slots = 0;
     for (int m = 0; m < B; ++m) {
         gvom_map* mp = maps[m];
         // window shift: the host copy of the origin moves now, in enqueue order
@@ -282,8 +288,14 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         sh.whole = whole;
         h.shift_prefix[m] = shift_total;
         shift_total += gvom::shift_units(g, d, whole);
+        int slot = -1;
+        sh.evict = gvom::take_slots(mp, 1, &slot);
+        h.evict_prefix[m] = evict_total;
+        evict_total += sh.evict ? gvom::evict_units(mp->s) : 0;
+        slots |= slot >= 0;
 
         h.ing[m] = ingest_args(mp, pts_dev[m], n[m], stride, b->tune.seg_len, T_ws + 12 * m, b->w);
+        h.ing[m].slot = slot;
         h.ray_prefix[m] = ray_blocks;
         ray_blocks += (n[m] + 255) / 256;
         h.ray_base[m] = ray_base;
@@ -309,6 +321,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     h.ray_prefix[B] = ray_blocks;
     h.col_prefix[B] = col_tasks;
     h.tile_prefix[B] = tiles;
+    h.evict_prefix[B] = evict_total;
+    h.hdr->evict_total = evict_total;
     h.hdr->B = B;
     h.hdr->shift_total = shift_total;
     h.hdr->ray_blocks = ray_blocks;
@@ -332,18 +346,20 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     const int do_extract = outs != nullptr;
 
     if (!(b->flags & GVOM_BATCH_GRAPH)) {
-        e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, st);
+        e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, st);
         if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, halo, st);
         return gvom::cuda_status(e);
     }
 
-    if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items) {
+    if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items ||
+        b->g_slots != slots) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
         const long long before = gvom_kernel_launches();
         e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t le = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, b->cap_stream);
+            cudaError_t le =
+                gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, b->cap_stream);
             if (le == cudaSuccess && do_extract) le = gvom::launch_batch_extract(t, b->max_maps, halo, b->cap_stream);
             e = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e == cudaSuccess) e = le;
@@ -357,6 +373,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         }
         b->g_extract = do_extract;
         b->g_halo = halo;
+        b->g_slots = slots;
         b->g_cap_items = b->w.cap_items;
         b->g_kernels = gvom_kernel_launches() - before;
         gvom::count_launch(-b->g_kernels);  // captured, not launched
@@ -397,6 +414,11 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
     const Geom g = geom_of(mp);
     const int rc = grow_items(b, total * max_segments_per_ray(g, mp->tune.seg_len), st);
     if (rc != GVOM_OK) return rc;
+    // with a scan buffer every scan takes a slot; the oldest go first
+    int slot[GVOM_MAX_SCAN_BUFFER];
+    const bool buffered = mp->cfg.scan_buffer > 0;
+    const unsigned long long evict = buffered ? take_slots(mp, k, slot) : 0ull;
+    const long long evict_total = evict ? evict_units(mp->s) : 0;
 
     const int cur = b->cur;
     cudaError_t e = cudaEventSynchronize(b->copied[cur]);
@@ -409,7 +431,10 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
         sh.s = mp->s;
         sh.g = g;
         h.shift_prefix[j] = 0;
+        sh.evict = j == 0 ? evict : 0ull;
+        h.evict_prefix[j] = j == 0 ? 0 : evict_total;
         h.ing[j] = ingest_args(mp, pts_dev[j], n[j], stride, mp->tune.seg_len, T_ws + 12 * j, b->w);
+        h.ing[j].slot = buffered ? slot[j] : -1;
         h.ray_prefix[j] = ray_blocks;
         ray_blocks += (n[j] + 255) / 256;
         h.ray_base[j] = ray_base;
@@ -426,6 +451,8 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
     h.hdr->ray_blocks = ray_blocks;
     h.hdr->col_tasks = 0;
     h.hdr->tiles = 0;
+    h.evict_prefix[k] = evict_total;
+    h.hdr->evict_total = evict_total;
     mp->scans += k;
     mp->points_in += total;
 
@@ -441,7 +468,8 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
     shape.block = mp->tune.march_block;
     shape.blocks_per_sm = mp->tune.march_blocks_per_sm;
     const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
-    return cuda_status(launch_batch_update(tables_at(b->d_tables, b->L), b->max_maps, max_ray_blocks, shared, shape, st));
+    return cuda_status(launch_batch_update(tables_at(b->d_tables, b->L), b->max_maps, max_ray_blocks, shared, shape,
+                                           evict != 0ull, buffered, st));
 }
 
 }  // namespace gvom

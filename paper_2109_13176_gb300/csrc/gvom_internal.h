@@ -18,12 +18,20 @@ struct Geom {
     int rx, ry, rz;
 };
 
-// Device state of one map.
+// Device state of one map. A map with a scan buffer (scan_buffer = K > 0)
+// also keeps its last K scans' own states in a ring of K slots ([K][V] per
+// array, same toroidal addressing); the main arrays always hold their
+// combination (counts summed, lowest return the minimum).
 struct MapState {
     uint32_t* hits;
     uint32_t* passes;
     float* minz;
     unsigned long long* counters;  // kCounters entries
+    uint32_t* ring_hits;           // K * V, or null
+    uint32_t* ring_passes;
+    float* ring_minz;
+    int ring_K;                    // 0: no buffer
+    uint32_t V;                    // voxels of the window (< 2^31)
 };
 
 // counters[kStatus] != 0: a bounded device wait of one of the map's kernels
@@ -54,6 +62,7 @@ struct IngestArgs {
     Geom g;
     MapState s;
     RayScratch w;
+    int slot;            // ring slot this scan also goes to, -1: none
 };
 
 // Launch shape of the segment walk (tunable).
@@ -80,6 +89,7 @@ struct BatchShift {
     Geom g;          // the new window
     int d[3];        // new - old origin (|d_k| < n_k unless whole)
     int whole;       // 1: clear the whole map
+    unsigned long long evict;  // ring slots emptied after the shift (bit j: slot j)
 };
 
 // Extraction of one map in a batch step.
@@ -102,6 +112,7 @@ struct BatchHeader {
     long long ray_blocks;    // 256-point blocks of the per-point pass
     long long col_tasks;     // 64-column warp tasks of the column pass
     long long tiles;         // pixel tiles of the plane-fit / cone pass
+    long long evict_total;   // 1024-voxel units of the eviction kernel
 };
 
 // Device pointers into one allocation of a batch's tables.
@@ -116,14 +127,18 @@ struct BatchTables {
     long long* col_prefix;    // [max_maps + 1], in tasks
     long long* tile_prefix;   // [max_maps + 1]
     int4* sensors;            // [max_maps], written on the device
+    long long* evict_prefix;  // [max_maps + 1], in 1024-voxel units
 };
 
 constexpr int kColTask = 64;       // columns per warp task of the batched column pass
 long long shift_units(const Geom& g, const int d[3], int whole);
 long long tiles_of(const ExtractParams& p);
 int tile_halo(const ExtractParams& p);
+// evict: run the eviction kernel after the shifts; slots: some map of the
+// step writes a ring slot.
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
-                                const MarchShape& shape, cudaStream_t st);
+                                const MarchShape& shape, bool evict, bool slots, cudaStream_t st);
+long long evict_units(const MapState& s);
 cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st);
 
 // Lookup-table export (export.cu): blocks of the count / write kernels and
@@ -140,7 +155,11 @@ bool valid_config(const gvom_config* c);
 void count_launch(long long n = 1);
 
 // Launchers (return the CUDA error of the launch).
+// Empties the map and, with a buffer, every ring slot.
 cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st);
+// Empties the ring slots of `mask`, taking their counts out of the map and
+// recomputing the lowest return where an emptied slot held it.
+cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_t st);
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st);
 cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st);
 // Segments a ray of the given window can have at most, for segment length L.
@@ -169,6 +188,8 @@ struct gvom_map {
     float* height_scratch;  // nx * ny, used when the caller asks for no height
     unsigned int* lut_counts;  // per-block counts of the lookup-table export
     struct gvom_batch* multi;  // tables for gvom_ingest_multi (created on first use)
+    int buf_head;                    // ring slot of the next scan
+    unsigned long long buf_occupied; // ring slots holding a scan
     gvom_tuning tune;
     long long scans;
     long long points_in;
@@ -183,6 +204,10 @@ bool valid_origin(const int64_t o[3]);
 ExtractParams extract_params(const gvom_map* m);
 bool valid_pose(const double T[12]);
 bool valid_tuning(const gvom_tuning* t);
+// Takes the ring slots of the map's next k scans (k <= K): returns the
+// occupied ones to empty first; slots[j] receives scan j's slot (-1 for a
+// map without a buffer).
+unsigned long long take_slots(gvom_map* m, int k, int* slots);
 // gvom_ingest_multi after validation (batch.cu).
 int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t* n, int stride, const double* T_ws,
                  cudaStream_t st);

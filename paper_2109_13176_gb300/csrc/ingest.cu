@@ -209,6 +209,11 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
             const uint32_t k = phys_index(g, ex, ey, ez);
             atomicAdd(a.s.hits + k, 1u);
             atomic_min_f32(a.s.minz + k, wz);
+            if (a.slot >= 0) {
+                const size_t o = (size_t)a.slot * a.s.V + k;
+                atomicAdd(a.s.ring_hits + o, 1u);
+                atomic_min_f32(a.s.ring_minz + o, wz);
+            }
             hit_in_window = 1;
         }
         RayFrame f;
@@ -439,7 +444,10 @@ __device__ __forceinline__ uint32_t walk_index(const Walk& w) {
 // record names its map, and descs / sensors hold each map's arguments and
 // quantised sensor position. Pass increments of lanes of different maps
 // never merge: lanes match on the full address.
-template <bool kBatch>
+//
+// kSlot: some ray's scan also goes to a ring slot of its map's scan buffer;
+// lanes then merge only within one slot.
+template <bool kBatch, bool kSlot>
 __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     const int lane = threadIdx.x & 31;
     const unsigned long long total_items = *a1.w.item_count;
@@ -458,6 +466,8 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
         bool live = false;
         unsigned int map = 0;
         uint32_t* passes = a1.s.passes;
+        uint32_t* spasses = nullptr;
+        if (kSlot && !kBatch) spasses = a1.s.ring_passes + (size_t)a1.slot * a1.s.V;
         unsigned long long item_visits = 0;
         if (idx < n_items) {
             const uint2 it = a1.w.items[idx];
@@ -468,6 +478,10 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 const int4 sq = sensors[map];
                 const int qo[3] = {sq.x, sq.y, sq.z};
                 passes = descs[map].s.passes;
+                if (kSlot) {
+                    const int sl = descs[map].slot;
+                    spasses = sl >= 0 ? descs[map].s.ring_passes + (size_t)sl * descs[map].s.V : nullptr;
+                }
                 live = walk_init(descs[map], qo, b, (int)it.y, w);
             } else {
                 live = walk_init(a1, qo1, b, (int)it.y, w);
@@ -488,12 +502,18 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 }
             }
             unsigned int peers;
-            if (kBatch)
+            if (kBatch && kSlot)
+                peers = __match_any_sync(
+                    0xffffffffu, inside ? (unsigned long long)(spasses ? spasses + key : passes + key) : 0ull);
+            else if (kBatch)
                 peers = __match_any_sync(0xffffffffu, inside ? (unsigned long long)(passes + key) : 0ull);
             else
                 peers = __match_any_sync(0xffffffffu, key);
             if (inside) {
-                if (lane == __ffs(peers) - 1) atomicAdd(passes + key, (uint32_t)__popc(peers));
+                if (lane == __ffs(peers) - 1) {
+                    atomicAdd(passes + key, (uint32_t)__popc(peers));
+                    if (kSlot && spasses) atomicAdd(spasses + key, (uint32_t)__popc(peers));
+                }
                 item_visits += 1;
             }
             if (!live) continue;
@@ -543,6 +563,44 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
     }
 }
 
+// Empties the ring slots of `mask` at voxel i: their counts leave the
+// combined state, and where an emptied slot held the combined lowest
+// return, that becomes the minimum over the slots that stay (+inf if none).
+__device__ __forceinline__ void evict_voxel(const MapState& s, unsigned long long mask, uint32_t i) {
+    uint32_t h = 0u, p = 0u;
+    bool gone = false;
+    for (int j = 0; j < s.ring_K; ++j) {
+        if (!((mask >> j) & 1ull)) continue;
+        const size_t o = (size_t)j * s.V + i;
+        const uint32_t hj = s.ring_hits[o], pj = s.ring_passes[o];
+        if ((hj | pj) == 0u) continue;
+        h += hj;
+        p += pj;
+        s.ring_hits[o] = 0u;
+        s.ring_passes[o] = 0u;
+        if (hj) {
+            const float mz = s.ring_minz[o];
+            s.ring_minz[o] = __int_as_float(0x7f800000);
+            gone |= mz == s.minz[i];
+        }
+    }
+    if ((h | p) != 0u) {
+        s.hits[i] -= h;
+        s.passes[i] -= p;
+    }
+    if (gone) {
+        float m = __int_as_float(0x7f800000);
+        for (int j = 0; j < s.ring_K; ++j)
+            if (!((mask >> j) & 1ull)) m = fminf(m, s.ring_minz[(size_t)j * s.V + i]);
+        s.minz[i] = m;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_evict(MapState s, unsigned long long mask) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < s.V; i += stride) evict_voxel(s, mask, i);
+}
+
 // Fill the state with the empty voxel: no hits, no passes, min height +inf.
 __global__ void k_init_state(uint32_t* __restrict__ hits, uint32_t* __restrict__ passes, float* __restrict__ minz,
                              long long V) {
@@ -572,6 +630,12 @@ __device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
     s.hits[k] = 0u;
     s.passes[k] = 0u;
     s.minz[k] = __int_as_float(0x7f800000);
+    for (int j = 0; j < s.ring_K; ++j) {
+        const size_t o = (size_t)j * s.V + k;
+        s.ring_hits[o] = 0u;
+        s.ring_passes[o] = 0u;
+        s.ring_minz[o] = __int_as_float(0x7f800000);
+    }
 }
 
 __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_xslab, long long n_units) {
@@ -705,7 +769,23 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays_batch(BatchTables t) {
     }
 }
 
+// Ring-slot eviction of all buffered maps of a batch step, one warp per
+// 1024 voxels of a map.
+__global__ void __launch_bounds__(256) k_evict_batch(BatchTables t) {
+    const int B = t.hdr->B;
+    const long long total = t.hdr->evict_total;
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < total; u += nwarps) {
+        const int m = find_map(t.evict_prefix, B, u);
+        const BatchShift& sh = t.sh[m];
+        const uint32_t v0 = (uint32_t)(u - t.evict_prefix[m]) * 1024u;
+        for (uint32_t v = v0 + lane; v < v0 + 1024u && v < sh.s.V; v += 32) evict_voxel(sh.s, sh.evict, v);
+    }
+}
+
 // Blocks of the persistent segment walk: every SM filled to its occupancy.
+template <bool kBatch, bool kSlot>
 int march_grid(const MarchShape& shape) {
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
@@ -713,7 +793,7 @@ int march_grid(const MarchShape& shape) {
     if (sms <= 0) sms = 1;
     int per_sm = shape.blocks_per_sm;
     if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<false>, shape.block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<kBatch, kSlot>, shape.block, 0);
         per_sm = nb > 0 ? nb : 1;
     }
     return sms * per_sm;
@@ -729,8 +809,10 @@ long long shift_units(const Geom& g, const int d[3], int whole) {
     return u;
 }
 
+long long evict_units(const MapState& s) { return ((long long)s.V + 1023) / 1024; }
+
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
-                                const MarchShape& shape, cudaStream_t st) {
+                                const MarchShape& shape, bool evict, bool slots, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -742,13 +824,21 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
     count_launch();
     k_shift_batch<<<(unsigned)sblocks, 256, 0, st>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (evict) {
+        count_launch();
+        k_evict_batch<<<(unsigned)(sms * 8), 256, 0, st>>>(t);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     long long rblocks = (long long)sms * 8;
     if (rblocks > max_ray_blocks) rblocks = max_ray_blocks > 0 ? max_ray_blocks : 1;
     count_launch();
     k_rays_batch<<<(unsigned)rblocks, kRaysBlock, 0, st>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
-    k_march<true><<<march_grid(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
+    if (slots)
+        k_march<true, true><<<march_grid<true, true>(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
+    else
+        k_march<true, false><<<march_grid<true, false>(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
     return cudaGetLastError();
 }
 
@@ -764,6 +854,19 @@ cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st) {
     if (blocks < 1) blocks = 1;
     count_launch();
     k_init_state<<<(unsigned)blocks, block, 0, st>>>(s.hits, s.passes, s.minz, V);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || s.ring_K == 0) return e;
+    count_launch();
+    k_init_state<<<152 * 16, block, 0, st>>>(s.ring_hits, s.ring_passes, s.ring_minz, V * s.ring_K);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_t st) {
+    if (s.ring_K == 0 || mask == 0ull) return cudaSuccess;
+    long long blocks = ((long long)s.V + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    count_launch();
+    k_evict<<<(unsigned)blocks, 256, 0, st>>>(s, mask);
     return cudaGetLastError();
 }
 
@@ -802,7 +905,10 @@ cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStre
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_march<false><<<march_grid(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
+    if (a.slot >= 0)
+        k_march<false, true><<<march_grid<false, true>(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
+    else
+        k_march<false, false><<<march_grid<false, false>(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ extern "C" int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t*
     p.slope_min_px = cfg->slope_min_px;
     p.neg_max_px = cfg->neg_max_px;
     p.neg_thresh = cfg->neg_thresh;
-    gvom::MapState s;
+    gvom::MapState s = {};
     s.hits = const_cast<uint32_t*>(hits_dev);  // read only
     s.passes = const_cast<uint32_t*>(passes_dev);
     s.minz = const_cast<float*>(minz_dev);

@@ -101,9 +101,10 @@ class Admission:
         return True
 
 
-def map_bytes(spec) -> int:
-    """Device memory of one map: 12 bytes per voxel plus 2D scratch and outputs."""
-    return 12 * spec.nx * spec.ny * spec.nz + (4 + 17) * spec.nx * spec.ny + 4096
+def map_bytes(spec, scan_buffer: int = 0) -> int:
+    """Device memory of one map: 12 bytes per voxel (and as much again per
+    slot of a scan buffer) plus 2D scratch and outputs."""
+    return 12 * (1 + scan_buffer) * spec.nx * spec.ny * spec.nz + (4 + 17) * spec.nx * spec.ny + 4096
 
 
 @dataclass
