@@ -54,6 +54,7 @@ typedef struct CUstream_st* gvom_stream_t;
 
 typedef enum gvom_status {
     GVOM_OK = 0,
+    GVOM_NOT_READY = 1,          /* gvom_pipeline_query: the scan is still in flight */
     GVOM_ERR_INVALID_ARG = -1,   /* a null pointer, size or parameter out of range */
     GVOM_ERR_OUT_OF_MEMORY = -2, /* device allocation failed */
     GVOM_ERR_CUDA = -3,          /* a CUDA call failed */
@@ -317,6 +318,44 @@ GVOM_API int gvom_batch_set_tuning(gvom_batch* batch, const gvom_tuning* tuning)
 GVOM_API int gvom_batch_step(gvom_batch* batch, struct gvom_map* const* maps, int32_t B, const double* vehicle_xyz,
                              const float* const* pts_dev, const int64_t* n, int32_t stride, const double* T_ws,
                              const gvom_maps_out* outs, gvom_stream_t stream);
+
+/* ---- Asynchronous scan pipeline ----------------------------------------
+ * The paper runs pointcloud processing and map processing as independent
+ * stages (Sec. III). A pipeline drives one map with three streams joined by
+ * events: upload (host points to a device staging slot), map (window shift
+ * for the vehicle position, ingest, column pass) and products (plane-fit /
+ * cone pass, then the products to host). Scan t's upload overlaps scan
+ * t-1's map stage, whose successor overlaps scan t-1's pixel pass and
+ * download; the map sees its scans in submission order. Three slots of
+ * staging and products: a submit blocks on the host until the scan three
+ * submissions back has finished. Results equal gvom_update followed by
+ * gvom_extract_maps for each scan in order. The map must not be used
+ * through other calls while scans are in flight. */
+typedef struct gvom_pipeline gvom_pipeline;
+
+/* 1 <= max_points <= GVOM_MAX_SCAN_POINTS / 4 (points per scan). Reserves
+ * the map's per-scan scratch for max_points. */
+GVOM_API int gvom_pipeline_create(struct gvom_map* map, int64_t max_points, gvom_pipeline** out);
+/* Waits for every scan in flight, then frees the pipeline (not the map). */
+GVOM_API void gvom_pipeline_destroy(gvom_pipeline* pipeline);
+/* Enqueues one scan: n points at pts_host (host memory; page-locked memory
+ * lets the copy overlap), stride 3 or 4 floats, pose T_ws, vehicle position
+ * vehicle_xyz (as gvom_update). out_host: NULL, or host buffers (page-locked
+ * for overlap; NULL members skipped) that receive this scan's products. The
+ * buffers must stay valid until the scan has finished. *ticket receives the
+ * scan's number (1, 2, ...). */
+GVOM_API int gvom_pipeline_submit(gvom_pipeline* pipeline, const double vehicle_xyz[3], const float* pts_host,
+                                  int64_t n, int32_t stride, const double T_ws[12], const gvom_maps_out* out_host,
+                                  int64_t* ticket);
+/* GVOM_OK once the scan's products are in host memory, GVOM_NOT_READY
+ * before; never blocks. */
+GVOM_API int gvom_pipeline_query(gvom_pipeline* pipeline, int64_t ticket);
+/* Blocks until the scan has finished. */
+GVOM_API int gvom_pipeline_wait(gvom_pipeline* pipeline, int64_t ticket);
+/* The device buffers holding the products of a scan (nx * ny each, layout of
+ * gvom_maps_out), valid from its completion until three more scans have
+ * been submitted. GVOM_ERR_INVALID_ARG once the slot has been reused. */
+GVOM_API int gvom_pipeline_products(gvom_pipeline* pipeline, int64_t ticket, gvom_maps_out* out_dev);
 
 /* Human-readable name of a status code (static storage). */
 GVOM_API const char* gvom_status_string(int status);

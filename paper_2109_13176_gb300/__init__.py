@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgvom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 GVOM_OK = 0
+GVOM_NOT_READY = 1
 GVOM_ERR_INVALID_ARG = -1
 GVOM_ERR_OUT_OF_MEMORY = -2
 GVOM_ERR_CUDA = -3
@@ -122,6 +123,12 @@ def load_library():
             "gvom_kernel_launches": ([], ctypes.c_int64),
             "gvom_ingest_multi": ([vp, i32, P(vp), P(i64), i32, P(ctypes.c_double), vp], ctypes.c_int),
             "gvom_export_lut": ([vp, vp, vp, vp, vp, i64, vp, vp], ctypes.c_int),
+            "gvom_pipeline_create": ([vp, i64, P(vp)], ctypes.c_int),
+            "gvom_pipeline_destroy": ([vp], None),
+            "gvom_pipeline_submit": ([vp, d3, vp, i64, i32, d3, P(gvom_maps_out), P(i64)], ctypes.c_int),
+            "gvom_pipeline_query": ([vp, i64], ctypes.c_int),
+            "gvom_pipeline_wait": ([vp, i64], ctypes.c_int),
+            "gvom_pipeline_products": ([vp, i64, P(gvom_maps_out)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -357,6 +364,93 @@ def gvom_batch_step(handle: int, map_handles, vehicle_xyz, points, T_ws, outs=No
         handle, maps, B, (ctypes.c_double * (3 * B))(*vx.tolist()), (ctypes.c_void_p * B)(*ptrs),
         (ctypes.c_int64 * B)(*ns), strides.pop(), (ctypes.c_double * (12 * B))(*T.tolist()),
         c_out, _stream_handle(stream)), "gvom_batch_step")
+
+
+def gvom_pipeline_create(map_handle: int, max_points: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().gvom_pipeline_create(map_handle, int(max_points), ctypes.byref(h)), "gvom_pipeline_create")
+    return h.value
+
+
+def gvom_pipeline_destroy(handle: int) -> None:
+    load_library().gvom_pipeline_destroy(handle)
+
+
+def _host_outs(outs):
+    if outs is None:
+        return None
+    return gvom_maps_out(*(outs[k].data_ptr() if outs.get(k) is not None else None
+                           for k in ("height", "density", "flags", "slope", "roughness")))
+
+
+def gvom_pipeline_submit(handle: int, vehicle_xyz, points, T_ws, outs=None) -> int:
+    """points: CPU float32 (n, 3|4) tensor (pinned for overlap); outs: None or a
+    dict of CPU tensors (pinned for overlap) for the products."""
+    if points.device.type != "cpu" or points.dtype.itemsize != 4 or not points.is_contiguous():
+        raise ValueError("points must be a contiguous float32 CPU tensor")
+    n, stride = int(points.shape[0]), int(points.shape[1])
+    t = ctypes.c_int64()
+    o = _host_outs(outs)
+    _check(load_library().gvom_pipeline_submit(handle, _d(vehicle_xyz, 3), points.data_ptr() if n else None, n,
+                                               stride, _T(T_ws), ctypes.byref(o) if o is not None else None,
+                                               ctypes.byref(t)), "gvom_pipeline_submit")
+    return t.value
+
+
+def gvom_pipeline_query(handle: int, ticket: int) -> bool:
+    rc = load_library().gvom_pipeline_query(handle, int(ticket))
+    if rc == GVOM_NOT_READY:
+        return False
+    _check(rc, "gvom_pipeline_query")
+    return True
+
+
+def gvom_pipeline_wait(handle: int, ticket: int) -> None:
+    _check(load_library().gvom_pipeline_wait(handle, int(ticket)), "gvom_pipeline_wait")
+
+
+def gvom_pipeline_products(handle: int, ticket: int) -> dict:
+    """Device pointers (ints) of a finished scan's products."""
+    o = gvom_maps_out()
+    _check(load_library().gvom_pipeline_products(handle, int(ticket), ctypes.byref(o)), "gvom_pipeline_products")
+    return {"height": o.height_dev, "density": o.density_dev, "flags": o.flags_dev, "slope": o.slope_dev,
+            "roughness": o.roughness_dev}
+
+
+class Pipeline:
+    """Asynchronous scan pipeline over one VoxelMap (see gvom_pipeline_*)."""
+
+    def __init__(self, vmap, max_points: int):
+        self.map = vmap
+        self.handle = gvom_pipeline_create(vmap.handle, max_points)
+
+    def alloc_host_outs(self):
+        import torch
+        nx, ny = self.map.shape[:2]
+        outs = {k: torch.empty((nx, ny), dtype=torch.float32, pin_memory=True)
+                for k in ("height", "density", "slope", "roughness")}
+        outs["flags"] = torch.empty((nx, ny), dtype=torch.uint8, pin_memory=True)
+        return outs
+
+    def submit(self, vehicle_xyz, points, T_ws, outs=None) -> int:
+        return gvom_pipeline_submit(self.handle, vehicle_xyz, points, T_ws, outs)
+
+    def query(self, ticket: int) -> bool:
+        return gvom_pipeline_query(self.handle, ticket)
+
+    def wait(self, ticket: int) -> None:
+        gvom_pipeline_wait(self.handle, ticket)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gvom_pipeline_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class MapBatch:

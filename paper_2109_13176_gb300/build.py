@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgvom.so")
-SOURCES = ["ingest.cu", "extract.cu", "export.cu", "api.cu", "batch.cu", "microbench.cu", "noalloc.cu"]
+SOURCES = ["ingest.cu", "extract.cu", "export.cu", "api.cu", "batch.cu", "pipeline.cu", "microbench.cu", "noalloc.cu"]
 HEADERS = ["gvom_internal.h", os.path.join("..", "..", "include", "gvom.h"),
            os.path.join("..", "..", "include", "gvom_microbench.h")]
 

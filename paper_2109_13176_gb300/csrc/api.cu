@@ -454,6 +454,7 @@ int64_t gvom_kernel_launches(void) { return (int64_t)gvom::g_launches.load(); }
 const char* gvom_status_string(int status) {
     switch (status) {
         case GVOM_OK: return "ok";
+        case GVOM_NOT_READY: return "not finished yet";
         case GVOM_ERR_INVALID_ARG: return "invalid argument";
         case GVOM_ERR_OUT_OF_MEMORY: return "out of device memory";
         case GVOM_ERR_CUDA: return "CUDA error";

@@ -73,6 +73,14 @@ def test_null_arguments_rejected(lib):
     ns = (ctypes.c_int64 * 1)(0)
     assert lib.gvom_ingest_multi(None, 1, ptrs, ns, 3, T, None) == gv.GVOM_ERR_INVALID_ARG
     assert lib.gvom_export_lut(None, None, None, None, None, 0, None, None) == gv.GVOM_ERR_INVALID_ARG
+    h = ctypes.c_void_p()
+    assert lib.gvom_pipeline_create(None, 10, ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG and h.value is None
+    t = ctypes.c_int64()
+    assert lib.gvom_pipeline_submit(None, T, None, 0, 3, T, None, ctypes.byref(t)) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_pipeline_query(None, 1) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_pipeline_wait(None, 1) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_pipeline_products(None, 1, None) == gv.GVOM_ERR_INVALID_ARG
+    lib.gvom_pipeline_destroy(None)  # no-op
     lib.gvom_destroy(None)  # no-op
 
 

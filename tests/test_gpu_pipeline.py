@@ -1,0 +1,98 @@
+"""The asynchronous scan pipeline (upload, map and products stages on three
+streams joined by events) gives, scan by scan, the same products as the
+plain path (gvom_update then gvom_extract_maps) on the same inputs, with
+several scans in flight."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_13176_gb300 import build
+    build.build()
+    import paper_2109_13176_gb300 as m
+    return m
+
+
+def run_both(gv, kw, scans, max_points):
+    plain = gv.VoxelMap(**kw)
+    piped = gv.VoxelMap(**kw)
+    pipe = gv.Pipeline(piped, max_points)
+    tickets, outs = [], []
+    for s in scans:
+        o = pipe.alloc_host_outs()
+        host_pts = torch.from_numpy(np.ascontiguousarray(s["points"], dtype=np.float32)).pin_memory()
+        tickets.append(pipe.submit(s["vehicle_xyz"], host_pts, s["T_ws"], o))
+        outs.append((o, host_pts))
+    pipe.wait(tickets[-1])
+    for t in tickets:
+        assert pipe.query(t)
+    for s, (o, _) in zip(scans, outs):
+        plain.update(s["vehicle_xyz"], torch.from_numpy(np.ascontiguousarray(s["points"], np.float32)).cuda(),
+                     s["T_ws"])
+        ref = plain.extract_maps()
+        torch.cuda.synchronize()
+        for k in ref:
+            np.testing.assert_array_equal(o[k].numpy(), ref[k].cpu().numpy(), err_msg=k)
+    for x, y in zip(plain.extract_voxels(), piped.extract_voxels()):
+        np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
+    pipe.close()
+    plain.close()
+    piped.close()
+
+
+def test_pipeline_full_size_sequence(gv):
+    cfg, scans = synth.sequence_scans(2, n_scans=5)
+    ms = cfg.map
+    kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    seq = [dict(points=s.points, T_ws=s.T_ws, vehicle_xyz=s.vehicle_xyz) for s in scans]
+    run_both(gv, kw, seq, max(len(s.points) for s in scans))
+
+
+@pytest.mark.parametrize("K", [0, 2])
+def test_pipeline_many_scans_in_flight(gv, K):
+    rng = np.random.default_rng(50 + K)
+    kw = dict(nx=96, ny=80, nz=32, res=0.2, neg_max_px=10, scan_buffer=K)
+    seq, centre = [], np.zeros(3)
+    for j in range(10):
+        centre = centre + rng.uniform(-0.6, 0.6, 3) * np.array([1, 1, 0.1])
+        n = 0 if j == 3 else int(rng.integers(100, 9000))
+        pts = rng.normal(scale=[4, 4, 0.6], size=(n, 3)).astype(np.float32)
+        if j % 2:
+            pts = np.concatenate([pts, np.ones((n, 1), np.float32)], axis=1)
+        th = rng.uniform(0, 2 * np.pi)
+        T = np.array([[math.cos(th), -math.sin(th), 0, centre[0]], [math.sin(th), math.cos(th), 0, centre[1]],
+                      [0, 0, 1.0, centre[2] + 1.0]])
+        seq.append(dict(points=pts, T_ws=T, vehicle_xyz=centre.copy()))
+    run_both(gv, kw, seq, 9000)
+
+
+def test_pipeline_tickets_and_slots(gv):
+    m = gv.VoxelMap(nx=32, ny=32, nz=16, res=0.2)
+    pipe = gv.Pipeline(m, 100)
+    pts = torch.zeros((10, 3), dtype=torch.float32).pin_memory()
+    T = np.array([[1.0, 0, 0, 0], [0, 1.0, 0, 0], [0, 0, 1.0, 1.0]])
+    t1 = pipe.submit((0, 0, 0), pts, T)
+    pipe.wait(t1)
+    prods = gv.gvom_pipeline_products(pipe.handle, t1)
+    assert all(v for v in prods.values())
+    ts = [pipe.submit((0, 0, 0), pts, T) for _ in range(3)]
+    pipe.wait(ts[-1])
+    assert pipe.query(t1)                       # finished long ago
+    with pytest.raises(gv.GvomError):
+        gv.gvom_pipeline_products(pipe.handle, t1)   # its slot has been reused
+    with pytest.raises(gv.GvomError):
+        pipe.wait(ts[-1] + 1)                   # not submitted
+    with pytest.raises(gv.GvomError):
+        pipe.submit((0, 0, 0), torch.zeros((101, 3), dtype=torch.float32), T)  # beyond max_points
+    pipe.close()
+    m.close()
