@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--retune", action="store_true", help="ignore cached tuning and search again")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--served-seconds", type=float, default=20.0, help="length of the replayed arrival stream")
+    ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
     return ap.parse_args()
 
 
@@ -329,6 +330,133 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush, stream, serial_e2e, hbm_peak):
+    """The widened rows on the plain-sequence workload: the asynchronous
+    pipeline end to end, the lookup-table export, a 10-scan buffer, and four
+    sensors per scan folded in one launch."""
+    ms = cfg.map
+    kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    n_steps = args.steps
+    ns = len(scans)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {}
+
+    # asynchronous pipeline: pinned host scan in, pinned host products out
+    m = gv.VoxelMap(**kw)
+    m.set_tuning(*tuning)
+    pipe = gv.Pipeline(m, max(int(p.shape[0]) for p in host_pts))
+    houts = [pipe.alloc_host_outs() for _ in range(3)]
+    t = 0
+    for k in range(args.warmup):
+        s = scans[k % ns]
+        t = pipe.submit(s.vehicle_xyz, host_pts[k % ns], s.T_ws, houts[k % 3])
+    pipe.wait(t)
+    r0 = m.stats()["rays_valid"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(n_steps):
+        k = args.warmup + i
+        s = scans[k % ns]
+        t = pipe.submit(s.vehicle_xyz, host_pts[k % ns], s.T_ws, houts[k % 3])
+    pipe.wait(t)
+    wall = time.perf_counter() - t0
+    rays = m.stats()["rays_valid"] - r0
+    out["pipeline_e2e"] = {"value": rays / wall, "unit": UNIT, "ms_per_scan": 1e3 * wall / n_steps,
+                           "vs_serial_e2e": rays / wall / serial_e2e, "depth": 3,
+                           "timing": "host wall clock from submit of the first scan to the last scan's products "
+                                     "in pinned host memory; steps overlap, so L2 is not flushed between them"}
+    pipe.close()
+
+    # lookup-table export of the map the pipeline left
+    V = ms.nx * ms.ny * ms.nz
+    lut = torch.empty(V, dtype=torch.int64, device="cuda")
+    dh = torch.empty(V, dtype=torch.int32, device="cuda")
+    dp = torch.empty(V, dtype=torch.int32, device="cuda")
+    dm = torch.empty(V, dtype=torch.float32, device="cuda")
+    n_occ = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(args.warmup):
+        gv.gvom_export_lut(m.handle, lut, dh, dp, dm, V, n_occ, stream)
+    lut_ms = []
+    for _ in range(n_steps):
+        flush()
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        gv.gvom_export_lut(m.handle, lut, dh, dp, dm, V, n_occ, stream)
+        e1.record(stream)
+        e1.synchronize()
+        lut_ms.append(e0.elapsed_time(e1))
+    occ = int(n_occ.item())
+    lut_bytes = 20 * V + 12 * occ
+    lut_s = statistics.mean(lut_ms) * 1e-3
+    out["lut_export"] = {"ms": 1e3 * lut_s, "voxels": V, "occupied": occ,
+                         "algorithmic_bytes": lut_bytes, "achieved_gbs": lut_bytes / lut_s / 1e9,
+                         "frac_hbm": lut_bytes / lut_s / 1e9 / hbm_peak if hbm_peak else None,
+                         "bytes_rule": "12 B/voxel read + 8 B/voxel table write + 12 B per occupied voxel",
+                         "kernels": 3}
+    m.close()
+
+    def timed_steps(mp, fn):
+        for k in range(args.warmup):
+            fn(k)
+        torch.cuda.synchronize()
+        r0 = mp.stats()["rays_valid"]
+        l0 = gv.gvom_kernel_launches()
+        ts = []
+        for i in range(n_steps):
+            flush()
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            fn(args.warmup + i)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ((mp.stats()["rays_valid"] - r0) / (sum(ts) * 1e-3), statistics.median(ts),
+                (gv.gvom_kernel_launches() - l0) / n_steps)
+
+    # 10-scan buffer: the same step on a map that holds its last 10 scans
+    mb = gv.VoxelMap(scan_buffer=10, **kw)
+    mb.set_tuning(*tuning)
+    ob = mb.alloc_maps()
+
+    def buffered_step(k):
+        s = scans[k % ns]
+        mb.update(s.vehicle_xyz, dev_pts[k % ns], s.T_ws)
+        mb.extract_maps(ob)
+    rate, med, launches = timed_steps(mb, buffered_step)
+    out["scan_buffer"] = {"K": 10, "value": rate, "unit": UNIT, "ms_per_step_median": med,
+                          "gpu_launches_per_step": launches,
+                          "note": "shift of all slots + eviction of the oldest slot + ingest into map and slot + extract"}
+    mb.close()
+
+    # four sensors per scan (each scan cut into four quarters, one pose each)
+    quarters = [[p[j * (p.shape[0] // 4):(j + 1) * (p.shape[0] // 4)] for j in range(4)] for p in dev_pts]
+    mm, mseq = gv.VoxelMap(**kw), gv.VoxelMap(**kw)
+    mm.set_tuning(*tuning)
+    mseq.set_tuning(*tuning)
+
+    def multi_step(k):
+        s = scans[k % ns]
+        mm.shift(mm.origin_for_pose(s.vehicle_xyz))
+        mm.ingest_multi(quarters[k % ns], [s.T_ws] * 4)
+
+    def seq_step(k):
+        s = scans[k % ns]
+        mseq.shift(mseq.origin_for_pose(s.vehicle_xyz))
+        for q in quarters[k % ns]:
+            mseq.ingest(q, s.T_ws)
+    r_m, med_m, l_m = timed_steps(mm, multi_step)
+    r_s, med_s, l_s = timed_steps(mseq, seq_step)
+    same = all(torch.equal(a, b) for a, b in zip(mm.extract_voxels(), mseq.extract_voxels()))
+    out["multi_sensor"] = {"sensors": 4, "value_one_launch": r_m, "value_sequential": r_s, "unit": UNIT,
+                           "ms_per_step_one_launch": med_m, "ms_per_step_sequential": med_s,
+                           "gpu_launches_per_step_one_launch": l_m, "gpu_launches_per_step_sequential": l_s,
+                           "state_identical": bool(same), "note": "shift + ingest only (no extraction)"}
+    mm.close()
+    mseq.close()
+    out["l2"] = "flushed between timed steps (256 MiB write), except the pipeline"
+    return out
+
+
 def run_served(args, gv, torch, inputs):
     """The served workload: real-time replay with continuous batching (latency),
     then all requests at once (capacity), batched vs one plain update per scan."""
@@ -505,6 +633,10 @@ def main():
         served = run_served(args, gv, torch, served_inputs)
 
     peaks, peak_kind = read_peaks()
+    next_rows = None
+    if not args.no_next_rows:
+        next_rows = run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush, stream,
+                                  rays_e2e / e2e_s, peaks.get("hbm_gbs"))
     red_peak = measure_red_peak(gv, torch)
     ingest_avg_s = statistics.mean(ingest_ms) * 1e-3
     atom_per_launch = (visits + 2 * hits) / args.steps
@@ -553,6 +685,7 @@ def main():
                    "search_us": tune_entry.get("us")},
         "batched": batched,
         "served": served,
+        "next_rows": next_rows,
     }
     print(json.dumps(line), flush=True)
     gmap.close()

@@ -323,10 +323,10 @@ GVOM_API int gvom_batch_step(gvom_batch* batch, struct gvom_map* const* maps, in
  * The paper runs pointcloud processing and map processing as independent
  * stages (Sec. III). A pipeline drives one map with three streams joined by
  * events: upload (host points to a device staging slot), map (window shift
- * for the vehicle position, ingest, column pass) and products (plane-fit /
- * cone pass, then the products to host). Scan t's upload overlaps scan
- * t-1's map stage, whose successor overlaps scan t-1's pixel pass and
- * download; the map sees its scans in submission order. Three slots of
+ * for the vehicle position, ingest, extraction of every product) and
+ * download (the products to host). Scan t's upload and scan t-1's download
+ * overlap scan t's compute; the map sees its scans in submission order.
+ * Three slots of
  * staging and products: a submit blocks on the host until the scan three
  * submissions back has finished. Results equal gvom_update followed by
  * gvom_extract_maps for each scan in order. The map must not be used

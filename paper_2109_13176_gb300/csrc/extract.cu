@@ -733,6 +733,17 @@ int sm_count() {
 
 }  // namespace
 
+cudaError_t allow_smem(const void* kernel, std::atomic<int>* cache, size_t bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (cache[dev].load(std::memory_order_relaxed) >= (int)bytes) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cache[dev].store((int)bytes, std::memory_order_relaxed);
+    return e;
+}
+
 int tile_halo(const ExtractParams& p) { return p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2; }
 
 long long tiles_of(const ExtractParams& p) {
@@ -749,7 +760,8 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
     if (e != cudaSuccess) return e;
     const size_t smem = slope_negative_smem_halo(max_halo);
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_slope_negative_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static std::atomic<int> cache[64];
+        e = allow_smem((const void*)k_slope_negative_batch, cache, smem);
         if (e != cudaSuccess) return e;
     }
     count_launch();
@@ -762,7 +774,8 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
     const long long cols = (long long)p.g.nx * p.g.ny;
     if ((p.g.nz & 3) == 0 && p.g.nz <= 256 && s.counters != nullptr) {
         const size_t smem = columns_tma_smem(p.g.nz);
-        cudaError_t e = cudaFuncSetAttribute(k_columns_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static std::atomic<int> cache[64];
+        cudaError_t e = allow_smem((const void*)k_columns_tma, cache, smem);
         if (e != cudaSuccess) return e;
         const long long chunks = (cols + kTmaCols - 1) / kTmaCols;
         long long blocks = (long long)sm_count() * 4;
@@ -796,8 +809,9 @@ cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, f
                                   uint8_t* flags, cudaStream_t st) {
     const size_t smem = slope_negative_smem(p);
     if (smem > 48 * 1024) {
+        static std::atomic<int> cache[64];
         const cudaError_t e =
-            cudaFuncSetAttribute(k_slope_negative, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_smem((const void*)k_slope_negative, cache, smem);
         if (e != cudaSuccess) return e;
     }
     const int tile = tile_edge(p);

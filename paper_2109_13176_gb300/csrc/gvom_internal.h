@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/gvom.h"
 
 namespace gvom {
@@ -146,6 +148,11 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
 long long lut_blocks(long long V);
 cudaError_t launch_export_lut(const MapState& s, const Geom& g, unsigned int* counts, long long* n_occupied,
                               long long* lut, uint32_t* dh, uint32_t* dp, float* dm, long long cap, cudaStream_t st);
+
+// Raises a kernel's dynamic shared memory limit to at least `bytes` on the
+// current device, calling the runtime only the first time a device needs a
+// larger limit (cache: one slot per device ordinal, 64 devices at most).
+cudaError_t allow_smem(const void* kernel, std::atomic<int>* cache, size_t bytes);
 
 // Whether a configuration is within the documented limits (include/gvom.h).
 bool valid_config(const gvom_config* c);

@@ -793,7 +793,14 @@ int march_grid(const MarchShape& shape) {
     if (sms <= 0) sms = 1;
     int per_sm = shape.blocks_per_sm;
     if (per_sm <= 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<kBatch, kSlot>, shape.block, 0);
+        // resident blocks per SM for 128- and 256-thread blocks, per device
+        static std::atomic<int> cache[64][2];
+        const int b = shape.block == 256 ? 1 : 0;
+        nb = dev >= 0 && dev < 64 ? cache[dev][b].load(std::memory_order_relaxed) : 0;
+        if (nb <= 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<kBatch, kSlot>, shape.block, 0);
+            if (nb > 0 && dev >= 0 && dev < 64) cache[dev][b].store(nb, std::memory_order_relaxed);
+        }
         per_sm = nb > 0 ? nb : 1;
     }
     return sms * per_sm;

@@ -4,16 +4,17 @@
 // joined by events:
 //
 //   upload    host points -> a device staging slot            (copy engine)
-//   map       window shift + ingest + column pass into a      (SMs)
-//             product slot
-//   products  plane-fit / cone pass on that slot's height     (SMs)
-//             map, then the products -> host                  (copy engine)
+//   map       window shift + ingest + column pass + plane-fit (SMs)
+//             / cone pass into a product slot
+//   download  the slot's products -> host                     (copy engine)
 //
-// Scan t's upload overlaps scan t-1's map stage, and scan t's map stage
-// overlaps scan t-1's pixel pass and download. Only the map stage touches
-// the voxel state, so the map sees its scans strictly in order. kDepth
-// slots of staging and products let up to kDepth scans be in flight; a
-// submit waits on the host for the scan that last used its slot.
+// Scan t's upload and scan t-1's download overlap scan t's compute. The
+// compute of consecutive scans stays on one stream: the ingest and column
+// kernels are persistent grids sized to fill every SM, and running another
+// scan's pixel pass beside them only delays their resident blocks. Only the
+// map stream touches the voxel state, so the map sees its scans strictly in
+// order. kDepth slots of staging and products let up to kDepth scans be in
+// flight; a submit waits on the host for the scan that last used its slot.
 #include <math.h>
 
 #include <new>
@@ -36,7 +37,7 @@ struct gvom_pipeline {
     float* slope[kDepth];
     float* rough[kDepth];
     uint8_t* flags[kDepth];
-    cudaEvent_t uploaded[kDepth], columns[kDepth], done[kDepth];
+    cudaEvent_t uploaded[kDepth], computed[kDepth], done[kDepth];
     long long ticket_of[kDepth];
     long long submitted;
 };
@@ -54,7 +55,7 @@ void gvom_pipeline_destroy(gvom_pipeline* p) {
         cudaFree(p->rough[k]);
         cudaFree(p->flags[k]);
         if (p->uploaded[k]) cudaEventDestroy(p->uploaded[k]);
-        if (p->columns[k]) cudaEventDestroy(p->columns[k]);
+        if (p->computed[k]) cudaEventDestroy(p->computed[k]);
         if (p->done[k]) cudaEventDestroy(p->done[k]);
     }
     if (p->up) cudaStreamDestroy(p->up);
@@ -83,7 +84,7 @@ int gvom_pipeline_create(gvom_map* map, int64_t max_points, gvom_pipeline** out)
         if (e == cudaSuccess) e = cudaMalloc(&p->rough[k], sizeof(float) * px);
         if (e == cudaSuccess) e = cudaMalloc(&p->flags[k], px);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->uploaded[k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->columns[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->computed[k], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done[k], cudaEventDisableTiming);
     }
     int rc = gvom::cuda_status(e);
@@ -125,10 +126,10 @@ int gvom_pipeline_submit(gvom_pipeline* p, const double vehicle_xyz[3], const fl
     if (rc != GVOM_OK) return rc;
     const gvom::ExtractParams ep = gvom::extract_params(p->map);
     e = gvom::launch_columns(p->map->s, ep, p->height[k], p->density[k], p->flags[k], p->mp);
-    if (e == cudaSuccess) e = cudaEventRecord(p->columns[k], p->mp);
-    // products stage
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->out, p->columns[k], 0);
-    if (e == cudaSuccess) e = gvom::launch_slope_negative(ep, p->height[k], p->slope[k], p->rough[k], p->flags[k], p->out);
+    if (e == cudaSuccess) e = gvom::launch_slope_negative(ep, p->height[k], p->slope[k], p->rough[k], p->flags[k], p->mp);
+    if (e == cudaSuccess) e = cudaEventRecord(p->computed[k], p->mp);
+    // download stage
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->out, p->computed[k], 0);
     const size_t px = (size_t)p->map->cfg.nx * p->map->cfg.ny;
     if (out_host) {
         const struct {
