@@ -14,10 +14,10 @@
 //  k_march  a persistent grid walks the segments. Each segment's first
 //           voxel is computed exactly from the rational time at which the
 //           major axis enters it, then the exact integer traversal runs to
-//           the segment's end and counts one pass per window voxel. Lanes
-//           that stand in the same voxel at the same step merge their
-//           increments (__match_any_sync), so neighbouring rays near the
-//           sensor cost one L2 atomic per warp.
+//           the segment's end and counts one pass per window voxel. Runs
+//           of neighbouring lanes that stand in the same voxel at the same
+//           step merge their increments (one shuffle and one ballot), so
+//           neighbouring rays near the sensor cost one L2 atomic per run.
 //
 // Counts are order-free sums, so the result is bit-identical to walking
 // every ray whole in one thread.
@@ -443,7 +443,7 @@ __device__ __forceinline__ uint32_t walk_index(const Walk& w) {
 // a1 carries only the shared scratch (work list and ray records), each ray
 // record names its map, and descs / sensors hold each map's arguments and
 // quantised sensor position. Pass increments of lanes of different maps
-// never merge: lanes match on the full address.
+// never merge: lanes compare the full address.
 //
 // kSlot: some ray's scan also goes to a ring slot of its map's scan buffer;
 // lanes then merge only within one slot.
@@ -501,18 +501,25 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                     if (inside) key = walk_index(w);
                 }
             }
-            unsigned int peers;
-            if (kBatch && kSlot)
-                peers = __match_any_sync(
-                    0xffffffffu, inside ? (unsigned long long)(spasses ? spasses + key : passes + key) : 0ull);
-            else if (kBatch)
-                peers = __match_any_sync(0xffffffffu, inside ? (unsigned long long)(passes + key) : 0ull);
-            else
-                peers = __match_any_sync(0xffffffffu, key);
+            // runs of neighbouring lanes in the same voxel merge their
+            // increments: the run's first lane adds the run's length
+            bool boundary;
+            if (kBatch) {
+                const unsigned long long kk =
+                    inside ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
+                const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
+                boundary = lane == 0 || prev != kk;
+            } else {
+                const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);  // every lane
+                boundary = lane == 0 || prev != key;
+            }
+            const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
             if (inside) {
-                if (lane == __ffs(peers) - 1) {
-                    atomicAdd(passes + key, (uint32_t)__popc(peers));
-                    if (kSlot && spasses) atomicAdd(spasses + key, (uint32_t)__popc(peers));
+                if (boundary) {
+                    const unsigned int after = starts & ~((2u << lane) - 1u);
+                    const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
+                    atomicAdd(passes + key, run);
+                    if (kSlot && spasses) atomicAdd(spasses + key, run);
                 }
                 item_visits += 1;
             }
