@@ -296,6 +296,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
 
         h.ing[m] = ingest_args(mp, pts_dev[m], n[m], stride, b->tune.seg_len, T_ws + 12 * m, b->w);
         h.ing[m].slot = slot;
+        h.ing[m].cnt_owner = m;
         h.ray_prefix[m] = ray_blocks;
         ray_blocks += (n[m] + 255) / 256;
         h.ray_base[m] = ray_base;
@@ -435,6 +436,7 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
         h.evict_prefix[j] = j == 0 ? 0 : evict_total;
         h.ing[j] = ingest_args(mp, pts_dev[j], n[j], stride, mp->tune.seg_len, T_ws + 12 * j, b->w);
         h.ing[j].slot = buffered ? slot[j] : -1;
+        h.ing[j].cnt_owner = 0;  // every entry is the same map
         h.ray_prefix[j] = ray_blocks;
         ray_blocks += (n[j] + 255) / 256;
         h.ray_base[j] = ray_base;

@@ -18,17 +18,30 @@ constexpr int kLutBlock = 256;
 constexpr int kLutPer = 4;                      // consecutive voxels per thread
 constexpr int kLutSpan = kLutBlock * kLutPer;   // voxels per block
 
-__device__ __forceinline__ uint32_t logical_to_phys(const Geom& g, long long i) {
-    const uint32_t cz = (uint32_t)i % (uint32_t)g.nz;  // i < V < 2^31
-    const uint32_t col = (uint32_t)i / (uint32_t)g.nz;
-    const uint32_t cy = col % (uint32_t)g.ny, cx = col / (uint32_t)g.ny;
-    int px = (int)cx + g.rx;
-    px -= (px >= g.nx) ? g.nx : 0;
-    int py = (int)cy + g.ry;
-    py -= (py >= g.ny) ? g.ny : 0;
-    int pz = (int)cz + g.rz;
-    pz -= (pz >= g.nz) ? g.nz : 0;
-    return ((uint32_t)px * g.ny + py) * (uint32_t)g.nz + pz;
+// Physical slots of the kLutPer consecutive logical voxels from i (those
+// past V are not used). When nz is a multiple of kLutPer the run lies in one
+// column, whose base takes one division.
+__device__ __forceinline__ void logical_to_phys(const Geom& g, uint32_t i, uint32_t (&k)[kLutPer]) {
+    const bool one_column = (g.nz % kLutPer) == 0;
+#pragma unroll
+    for (int j = 0; j < kLutPer; ++j) {
+        if (j > 0 && one_column) {
+            int pz = (int)(k[0] % (uint32_t)g.nz) + j;  // k[0] = base + pz0
+            k[j] = k[0] + j - (pz >= g.nz ? (uint32_t)g.nz : 0u);
+            continue;
+        }
+        const uint32_t ij = i + (uint32_t)j;  // i < V < 2^31
+        const uint32_t cz = ij % (uint32_t)g.nz;
+        const uint32_t col = ij / (uint32_t)g.nz;
+        const uint32_t cy = col % (uint32_t)g.ny, cx = col / (uint32_t)g.ny;
+        int px = (int)cx + g.rx;
+        px -= (px >= g.nx) ? g.nx : 0;
+        int py = (int)cy + g.ry;
+        py -= (py >= g.ny) ? g.ny : 0;
+        int pz = (int)cz + g.rz;
+        pz -= (pz >= g.nz) ? g.nz : 0;
+        k[j] = ((uint32_t)px * g.ny + py) * (uint32_t)g.nz + pz;
+    }
 }
 
 // Exclusive block-wide scan of one value per thread (kLutBlock threads).
@@ -60,9 +73,13 @@ __global__ void __launch_bounds__(kLutBlock) k_lut_count(MapState s, Geom g, lon
     __shared__ unsigned int total;
     const long long i0 = (long long)blockIdx.x * kLutSpan + (long long)threadIdx.x * kLutPer;
     unsigned int c = 0;
+    if (i0 < V) {
+        uint32_t k_[kLutPer];
+        logical_to_phys(g, (uint32_t)i0, k_);
 #pragma unroll
-    for (int k = 0; k < kLutPer; ++k)
-        if (i0 + k < V) c += s.hits[logical_to_phys(g, i0 + k)] != 0u ? 1u : 0u;
+        for (int k = 0; k < kLutPer; ++k)
+            if (i0 + k < V) c += s.hits[k_[k]] != 0u ? 1u : 0u;
+    }
     block_exclusive(c, warp_sums, &total);
     if (threadIdx.x == 0) counts[blockIdx.x] = total;
 }
@@ -110,33 +127,38 @@ __global__ void __launch_bounds__(kLutBlock)
     __shared__ unsigned int total;
     const long long i0 = (long long)blockIdx.x * kLutSpan + (long long)threadIdx.x * kLutPer;
     uint32_t k_[kLutPer];
-    uint32_t h_[kLutPer];
+    uint32_t h_[kLutPer], p_[kLutPer];
+    float m_[kLutPer];
     unsigned int c = 0;
+    if (i0 < V) logical_to_phys(g, (uint32_t)i0, k_);
+    // every load before the block scan, so they are in flight together
 #pragma unroll
     for (int k = 0; k < kLutPer; ++k) {
-        k_[k] = 0;
         h_[k] = 0;
+        p_[k] = 0;
+        m_[k] = 0.0f;
         if (i0 + k < V) {
-            k_[k] = logical_to_phys(g, i0 + k);
             h_[k] = s.hits[k_[k]];
-            c += h_[k] != 0u ? 1u : 0u;
+            p_[k] = s.passes[k_[k]];
+            m_[k] = s.minz[k_[k]];
         }
     }
+#pragma unroll
+    for (int k = 0; k < kLutPer; ++k) c += h_[k] != 0u ? 1u : 0u;
     long long idx = (long long)prefix[blockIdx.x] + block_exclusive(c, warp_sums, &total);
 #pragma unroll
     for (int k = 0; k < kLutPer; ++k) {
         if (i0 + k >= V) break;
-        const uint32_t pm = s.passes[k_[k]];
         if (h_[k] != 0u) {
             lut[i0 + k] = idx;
             if (idx < cap) {
                 d_hits[idx] = h_[k];
-                d_passes[idx] = pm;
-                d_minz[idx] = s.minz[k_[k]];
+                d_passes[idx] = p_[k];
+                d_minz[idx] = m_[k];
             }
             idx += 1;
         } else {
-            lut[i0 + k] = -1 - (long long)pm;
+            lut[i0 + k] = -1 - (long long)p_[k];
         }
     }
 }

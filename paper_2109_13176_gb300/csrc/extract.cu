@@ -253,19 +253,19 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
 // ---- TMA-staged column pass (nz % 4 == 0) ----------------------------------
 //
 // The map state is column-major (z fastest), so C consecutive physical
-// columns of hits (and of lowest returns) are one contiguous run of
-// C * nz * 4 bytes. One thread per block streams such runs into a ring of
-// shared-memory stages with 1D bulk copies (cp.async.bulk, completion on an
-// mbarrier per stage), kStages chunks ahead; all warps reduce the chunk in
-// place, LPC = 8 lanes per column. Passes are read from global memory only
-// for the voxels of the obstacle band. Every mbarrier wait is bounded; a
-// wait that gives up sets the map's status word and the block returns after
-// draining the copies it issued. Used for nz % 4 == 0 and nz <= 256 (three
-// stages of 2 x 32 columns fit shared memory; each stage's transaction count
-// stays below the mbarrier's 2^20 bytes).
+// columns of hits (and of passes, and of lowest returns) are one contiguous
+// run of C * nz * 4 bytes. One thread per block streams such runs into a
+// ring of shared-memory stages with 1D bulk copies (cp.async.bulk,
+// completion on an mbarrier per stage), kStages chunks ahead; all warps
+// reduce the chunk in place, LPC = 8 lanes per column, with no global load
+// on the reduction's path. Every mbarrier wait is bounded; a wait that gives
+// up sets the map's status word and the block returns after draining the
+// copies it issued. Used for nz % 4 == 0 and nz <= 256 (two stages of
+// 3 x 32 columns fit shared memory; each stage's transaction count stays
+// below the mbarrier's 2^20 bytes).
 
 constexpr int kTmaCols = 32;      // columns per chunk
-constexpr int kTmaStages = 3;
+constexpr int kTmaStages = 2;
 constexpr int kTmaBlock = 256;
 constexpr unsigned kSpinLimit = 1u << 22;
 
@@ -300,17 +300,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
-size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 2 * kTmaCols * nz * sizeof(float); }
+size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 3 * kTmaCols * nz * sizeof(float); }
 
 // Starts the copies of chunk `chunk` into `stage`.
 __device__ __forceinline__ void tma_issue(const MapState& s, int nz, long long ncols, long long chunk, int stage,
-                                          unsigned long long* bars, uint32_t* hb, float* mb) {
+                                          unsigned long long* bars, uint32_t* hb, float* mb, uint32_t* pb) {
     const long long c0 = chunk * kTmaCols;
     const long long cols = ncols - c0 < kTmaCols ? ncols - c0 : kTmaCols;
     const unsigned bytes = (unsigned)(cols * nz * 4);
-    mbar_expect_tx(&bars[stage], 2u * bytes);
+    mbar_expect_tx(&bars[stage], 3u * bytes);
     bulk_load(hb + (size_t)stage * kTmaCols * nz, s.hits + c0 * nz, bytes, &bars[stage]);
     bulk_load(mb + (size_t)stage * kTmaCols * nz, s.minz + c0 * nz, bytes, &bars[stage]);
+    bulk_load(pb + (size_t)stage * kTmaCols * nz, s.passes + c0 * nz, bytes, &bars[stage]);
 }
 
 __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm);
     uint32_t* hb = reinterpret_cast<uint32_t*>(sm + 128);
     float* mb = reinterpret_cast<float*>(hb + (size_t)kTmaStages * kTmaCols * nz);
+    uint32_t* pb = reinterpret_cast<uint32_t*>(mb + (size_t)kTmaStages * kTmaCols * nz);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & 7;                      // lane within the column's 8-lane group
     const Band band = make_band(p.obs_min_h, p.obs_max_h);
@@ -338,7 +340,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
     if (tid == 0)
         for (int st = 0; st < kTmaStages; ++st) {
             const long long c = blockIdx.x + (long long)st * gridDim.x;
-            if (c < nchunks) tma_issue(s, nz, ncols, c, st, bars, hb, mb);
+            if (c < nchunks) tma_issue(s, nz, ncols, c, st, bars, hb, mb, pb);
         }
 
     int k = 0;
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
         if (s_fail) break;
         const uint32_t* hst = hb + (size_t)st * kTmaCols * nz;
         const float* mst = mb + (size_t)st * kTmaCols * nz;
+        const uint32_t* pst = pb + (size_t)st * kTmaCols * nz;
         const long long c0 = c * kTmaCols;
         // 8 warps x 4 columns = the chunk's 32 columns
         const int j = warp * 4 + (lane >> 3);
@@ -379,13 +382,15 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
             for (int v = sub; v < nv; v += 8) {
                 const uint4 a = hv4[v];
                 const float4 b = mv4[v];
+                const uint4 pm = reinterpret_cast<const uint4*>(pst + (size_t)j * nz)[v];
                 const uint32_t hs[4] = {a.x, a.y, a.z, a.w};
                 const float ms[4] = {b.x, b.y, b.z, b.w};
+                const uint32_t ps[4] = {pm.x, pm.y, pm.z, pm.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (hs[q] != 0u && in_band(ms[q], h, band)) {
                         H += hs[q];
-                        M += s.passes[pc * nz + 4 * v + q];
+                        M += ps[q];
                         inband = true;
                     }
             }
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
         __syncthreads();  // every warp is done with this stage
         if (tid == 0) {
             const long long c2 = c + (long long)kTmaStages * gridDim.x;
-            if (c2 < nchunks) tma_issue(s, nz, ncols, c2, st, bars, hb, mb);
+            if (c2 < nchunks) tma_issue(s, nz, ncols, c2, st, bars, hb, mb, pb);
         }
     }
     if (s_fail && tid == 0) {
@@ -778,7 +783,15 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
         cudaError_t e = allow_smem((const void*)k_columns_tma, cache, smem);
         if (e != cudaSuccess) return e;
         const long long chunks = (cols + kTmaCols - 1) / kTmaCols;
-        long long blocks = (long long)sm_count() * 4;
+        // persistent grid: only as many blocks per SM as its shared memory
+        // holds at once (1 KB of each block's share is reserved)
+        int dev = 0, smem_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        long long per_sm = (long long)smem_sm / (long long)(smem + 1024);
+        if (per_sm > 4) per_sm = 4;
+        if (per_sm < 1) per_sm = 1;
+        long long blocks = (long long)sm_count() * per_sm;
         if (blocks > chunks) blocks = chunks;
         count_launch();
         k_columns_tma<<<(unsigned)blocks, kTmaBlock, smem, st>>>(s, p, height, density, flags);

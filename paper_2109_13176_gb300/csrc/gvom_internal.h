@@ -65,6 +65,7 @@ struct IngestArgs {
     MapState s;
     RayScratch w;
     int slot;            // ring slot this scan also goes to, -1: none
+    int cnt_owner;       // batch entry whose counters this entry's visits go to
 };
 
 // Launch shape of the segment walk (tunable).

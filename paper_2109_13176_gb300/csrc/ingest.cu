@@ -447,6 +447,25 @@ __device__ __forceinline__ uint32_t walk_index(const Walk& w) {
 //
 // kSlot: some ray's scan also goes to a ring slot of its map's scan buffer;
 // lanes then merge only within one slot.
+// Adds each lane's pending visits to the counters of entry `own` (the map's
+// own when descs is null): one atomic per warp when every lane holds the
+// same entry, else one per lane. All lanes call it.
+__device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestArgs* descs, unsigned int own,
+                                             unsigned long long& visits) {
+    int same = 0;
+    __match_all_sync(0xffffffffu, own, &same);
+    unsigned long long* cnt = own == 0xffffffffu ? nullptr : (descs ? descs[own].s.counters : a1.s.counters);
+    if (same) {
+        unsigned long long v = visits;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && cnt && v) atomicAdd(cnt + kPassVisits, v);
+    } else if (cnt && visits) {
+        atomicAdd(cnt + kPassVisits, visits);
+    }
+    visits = 0;
+}
+
 template <bool kBatch, bool kSlot>
 __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     const int lane = threadIdx.x & 31;
@@ -459,12 +478,17 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
     int qo1[3] = {0, 0, 0};
     if (!kBatch) block_sensor(a1, qo1);  // the work list only holds rays of a quantisable sensor
 
+    // pass visits not yet added to the counters of entry `own` (per lane;
+    // in batch mode the pending entry changes only when a lane's item belongs
+    // to a map with other counters, so several entries of one map add once)
     unsigned long long visits = 0;
+    unsigned int own = kBatch ? 0xffffffffu : 0u;
     for (long long base = gw * 32; base < n_items; base += nwarps * 32) {
         const long long idx = base + lane;
         Walk w;
         bool live = false;
         unsigned int map = 0;
+        unsigned int own_item = own;  // entry owning the counters of this lane's item's map
         uint32_t* passes = a1.s.passes;
         uint32_t* spasses = nullptr;
         if (kSlot && !kBatch) spasses = a1.s.ring_passes + (size_t)a1.slot * a1.s.V;
@@ -478,6 +502,7 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 const int4 sq = sensors[map];
                 const int qo[3] = {sq.x, sq.y, sq.z};
                 passes = descs[map].s.passes;
+                own_item = (unsigned int)descs[map].cnt_owner;
                 if (kSlot) {
                     const int sl = descs[map].slot;
                     spasses = sl >= 0 ? descs[map].s.ring_passes + (size_t)sl * descs[map].s.V : nullptr;
@@ -545,29 +570,14 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
             // so it passes the window exactly at its exit voxel)
             if (w.cA == w.exitA || w.cB == w.exitB) live = false;
         }
-        if (kBatch) {
-            // counters per map: one atomic per warp when all lanes share a map
-            int all_same = 0;
-            __match_all_sync(0xffffffffu, map, &all_same);
-            if (all_same) {
-                unsigned long long v = item_visits;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0 && v) atomicAdd(descs[map].s.counters + kPassVisits, v);
-            } else if (item_visits) {
-                atomicAdd(descs[map].s.counters + kPassVisits, item_visits);
-            }
-        } else {
-            visits += item_visits;
+        if (kBatch && __any_sync(0xffffffffu, own_item != own)) {
+            flush_visits(a1, descs, own, visits);
+            own = own_item;
         }
+        visits += item_visits;
     }
 
-    if (!kBatch) {
-        // Counter: one atomic per warp of the persistent grid.
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) visits += __shfl_xor_sync(0xffffffffu, visits, o);
-        if (lane == 0 && visits) atomicAdd(a1.s.counters + kPassVisits, visits);
-    }
+    flush_visits(a1, descs, own, visits);
 }
 
 // Empties the ring slots of `mask` at voxel i: their counts leave the
@@ -603,9 +613,30 @@ __device__ __forceinline__ void evict_voxel(const MapState& s, unsigned long lon
     }
 }
 
+// Four consecutive voxels from i (a multiple of 4, V % 4 == 0): one 16-byte
+// load per array and slot finds the common case, four voxels that no
+// emptied slot touched.
+__device__ __forceinline__ void evict_quad(const MapState& s, unsigned long long mask, uint32_t i) {
+    uint32_t any = 0u;
+    for (int j = 0; j < s.ring_K; ++j) {
+        if (!((mask >> j) & 1ull)) continue;
+        const size_t o = (size_t)j * s.V + i;
+        const uint4 h = *reinterpret_cast<const uint4*>(s.ring_hits + o);
+        const uint4 p = *reinterpret_cast<const uint4*>(s.ring_passes + o);
+        any |= h.x | h.y | h.z | h.w | p.x | p.y | p.z | p.w;
+    }
+    if (any == 0u) return;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) evict_voxel(s, mask, i + e);
+}
+
 __global__ void __launch_bounds__(256) k_evict(MapState s, unsigned long long mask) {
-    const uint32_t stride = gridDim.x * blockDim.x;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < s.V; i += stride) evict_voxel(s, mask, i);
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((s.V & 3u) == 0u) {
+        if (4u * t < s.V) evict_quad(s, mask, 4u * t);
+    } else if (t < s.V) {
+        evict_voxel(s, mask, t);
+    }
 }
 
 // Fill the state with the empty voxel: no hits, no passes, min height +inf.
@@ -787,7 +818,11 @@ __global__ void __launch_bounds__(256) k_evict_batch(BatchTables t) {
         const int m = find_map(t.evict_prefix, B, u);
         const BatchShift& sh = t.sh[m];
         const uint32_t v0 = (uint32_t)(u - t.evict_prefix[m]) * 1024u;
-        for (uint32_t v = v0 + lane; v < v0 + 1024u && v < sh.s.V; v += 32) evict_voxel(sh.s, sh.evict, v);
+        if ((sh.s.V & 3u) == 0u) {
+            for (uint32_t v = v0 + 4u * lane; v < v0 + 1024u && v < sh.s.V; v += 128) evict_quad(sh.s, sh.evict, v);
+        } else {
+            for (uint32_t v = v0 + lane; v < v0 + 1024u && v < sh.s.V; v += 32) evict_voxel(sh.s, sh.evict, v);
+        }
     }
 }
 
@@ -877,8 +912,8 @@ cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st) {
 
 cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_t st) {
     if (s.ring_K == 0 || mask == 0ull) return cudaSuccess;
-    long long blocks = ((long long)s.V + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const long long threads = (s.V & 3u) == 0u ? (long long)s.V / 4 : (long long)s.V;
+    const long long blocks = (threads + 255) / 256;
     count_launch();
     k_evict<<<(unsigned)blocks, 256, 0, st>>>(s, mask);
     return cudaGetLastError();
