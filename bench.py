@@ -71,8 +71,8 @@ def gen_workers() -> int:
 
 def make_inputs(rank: int):
     import synth
-    seed = synth.SEED_BASE + 2 + 1000 * rank
-    cfg, scans = synth.sequence_scans(2, seed=seed, workers=gen_workers())
+    seed = synth.SEEDS["sequence"] + 1000 * rank
+    cfg, scans = synth.sequence_scans("sequence", seed=seed, workers=gen_workers())
     return cfg, scans
 
 
@@ -87,13 +87,13 @@ SERVED_WORKLOAD = ("served: 32 robots, mixed sensors (16/64/128 beams) and maps 
 
 def make_served_inputs(rank: int, seconds: float):
     import synth
-    return synth.served_requests(n_robots=32, duration_s=seconds, pool=4, seed=synth.SEED_BASE + 5 + 1000 * rank,
+    return synth.served_requests(n_robots=32, duration_s=seconds, pool=4, seed=synth.SEEDS["served"] + 1000 * rank,
                                  workers=gen_workers())
 
 
 def make_batched_inputs(rank: int, n_maps: int):
     import synth
-    return synth.batched_scans(n_maps=n_maps, n_steps=2, seed=synth.SEED_BASE + 4 + 1000 * rank,
+    return synth.batched_scans(n_maps=n_maps, n_steps=2, seed=synth.SEEDS["batched"] + 1000 * rank,
                                workers=gen_workers())
 
 
@@ -669,7 +669,7 @@ def main():
                     "ingest_avg": 1e3 * ingest_avg_s, "extract_avg": 1e3 * extract_avg_s},
         "roofline": {"kernel": "k_ingest", "bound": "l2_atomic", "achieved": achieved / 1e9,
                      "peak": red_peak / 1e9, "unit": "Gatomic/s", "frac": achieved / red_peak,
-                     "traffic": profile_traffic("k_ingest", "config2"),
+                     "traffic": profile_traffic("k_ingest", "plain_sequence"),
                      "peak_source": "measured in this run: scattered 32-bit reduction atomics over 64 MiB (gvom_microbench_red)",
                      "algorithmic": "pass visits + 2 atomics per in-window hit, per launch"},
         "roofline_extract": {"kernels": "k_columns + k_slope_negative", "bound": "hbm",

@@ -16,11 +16,12 @@ from .scenes import (  # noqa: F401
     MapSpec,
     Scan,
     Scene,
-    config1_scan,
+    single_scan,
     sequence_config,
     sequence_scans,
     batched_scans,
     served_requests,
-    CONFIGS,
+    WORKLOADS,
     SEED_BASE,
+    SEEDS,
 )

@@ -1,29 +1,29 @@
 """Scene, trajectory and lidar models (inputs only; see the package docstring).
 
-Recipes (seed = SEED_BASE + config number, sub-seeds by map/robot index):
+Recipes (seed = SEEDS[workload], sub-seeds by map/robot index):
 
-1. Single scan: 16-beam lidar (+-15 deg, 1024 columns), ground z = tan(5 deg) x,
+single_scan: 16-beam lidar (+-15 deg, 1024 columns), ground z = tan(5 deg) x,
    two 1 x 1 x 2 m boxes at (5, 3) and (-4, -5), a ditch 2 m wide (x in
    [7, 9]) and 0.8 m deep spanning y in [-6, 6], and 2,000 vegetation points
    uniform in [-6, -3] x [2, 5] x [g, g + 1] (g = ground height) appended to
    the 16,384-point organised scan. Sensor at (0, 0, 1.5), identity pose.
-2. Sequence: 64-beam lidar (+-16.6 deg, 2048 columns), 20 scans at 10 Hz,
+sequence: 64-beam lidar (+-16.6 deg, 2048 columns), 20 scans at 10 Hz,
    4.5 m/s along y = 0.557 sin(2 pi x / 40) (heading follows the tangent,
    +-5 deg), pitch 5 deg sin(2 pi t / 2 s); terrain = 4 seeded sinusoid
    octaves (amplitude 0.5 m halving, wavelength 40 m halving), 30 boxes
    (footprint 0.5-2 m, height 0.5-2.5 m) and 10 ditches (width 1-3 m, depth
    0.5-1.5 m, length 3-10 m).
-3. High speed: 128-beam lidar (+-22.5 deg, 2048 columns), 40 scans at 12 m/s,
+high_speed: 128-beam lidar (+-22.5 deg, 2048 columns), 40 scans at 12 m/s,
    the same generator plus two roughness octaves (0.15 m at 2.5 m, 0.075 m
    at 1.25 m) and vegetation clusters (radius 1-2 m, 0.5-1.5 m tall) where
    20 % of the rays entering a cluster return inside it at a uniform depth
    and the rest pass through.
-4. Batched: 64 maps of the sequence kind, each with its own terrain and
+batched: 64 maps of the sequence kind, each with its own terrain and
    trajectory (terrain modelled 70 m around the route; beyond it the ground
    continues at the edge height); each map's scan per step is a seeded
    random subset (scan order kept) of a 128 x 2048 scan, of size
    floor(exp U(ln 8192, ln 262144)).
-5. Served: 32 robots with mixed sensors (16/64/128 beams) and maps, arrivals
+served: 32 robots with mixed sensors (16/64/128 beams) and maps, arrivals
    with exponential inter-arrival times (mean 100 ms), over a stream of
    given length; each robot draws its scans from a small pool of consecutive
    scans of its own trajectory.
@@ -39,6 +39,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SEED_BASE = 13176
+SEEDS = {"single_scan": SEED_BASE + 1, "sequence": SEED_BASE + 2, "high_speed": SEED_BASE + 3,
+         "batched": SEED_BASE + 4, "served": SEED_BASE + 5}
 
 
 @dataclass(frozen=True)
@@ -299,8 +301,8 @@ def scan_from_pose(scene: Scene, lidar: LidarSpec, T_ws: np.ndarray, vehicle_xyz
     return Scan(points=pts, T_ws=T_ws, vehicle_xyz=np.asarray(vehicle_xyz, dtype=np.float64), t=t)
 
 
-# --- configuration 1 -------------------------------------------------------
-def config1_scene() -> Scene:
+# --- the single-scan test scene ----------------------------------------------
+def single_scan_scene() -> Scene:
     tilt = math.tan(math.radians(5.0))
     sc = Scene(tilt_x=tilt, raster=0.05)
     sc.ditches.append(Ditch(cx=8.0, cy=0.0, hl=1.0, hw=6.0, yaw=0.0, depth=0.8))
@@ -311,10 +313,10 @@ def config1_scene() -> Scene:
     return sc
 
 
-def config1_scan(seed: int = SEED_BASE + 1) -> Scan:
+def single_scan(seed: int | None = None) -> Scan:
     """16,384-beam organised scan plus 2,000 appended vegetation points."""
-    rng = np.random.default_rng(seed)
-    sc = config1_scene()
+    rng = np.random.default_rng(SEEDS["single_scan"] if seed is None else seed)
+    sc = single_scan_scene()
     lidar = LidarSpec(16, 1024, 15.0)
     T = pose_matrix((0.0, 0.0, 0.0), 0.0, 0.0)
     s = scan_from_pose(sc, lidar, T, (0.0, 0.0, 0.0), rng)
@@ -328,7 +330,7 @@ def config1_scan(seed: int = SEED_BASE + 1) -> Scan:
     return s
 
 
-# --- sequence scenes (configurations 2-5) ----------------------------------
+# --- sequence scenes (sequence, high_speed, batched, served) ---------------
 def random_scene(rng, x_range, y_range, rough: float = 0.0, veg_clusters: int = 0,
                  n_boxes: int = 30, n_ditches: int = 10, raster: float = 0.1,
                  path=None) -> Scene:
@@ -383,13 +385,15 @@ class SequenceConfig:
     rate_hz: float = 10.0
 
 
-def sequence_config(k: int) -> SequenceConfig:
-    if k == 2:
+def sequence_config(name: str) -> SequenceConfig:
+    """The sequence workloads: "sequence" (64-beam, 256 x 256 x 64 @ 0.2 m) and
+    "high_speed" (128-beam, 512 x 512 x 64 @ 0.1 m)."""
+    if name == "sequence":
         return SequenceConfig(MapSpec(256, 256, 64, 0.2), LidarSpec(64, 2048, 16.6), 20, 4.5)
-    if k == 3:
+    if name == "high_speed":
         return SequenceConfig(MapSpec(512, 512, 64, 0.1), LidarSpec(128, 2048, 22.5), 40, 12.0,
                               rough=0.15, veg_clusters=60)
-    raise ValueError(k)
+    raise ValueError(name)
 
 
 def _path_y(x):
@@ -422,8 +426,8 @@ def make_sequence_scene(cfg: SequenceConfig, rng, yaw0: float = 0.0, extent: flo
 
 
 def _sequence_chunk(args):
-    k, seed, steps = args
-    cfg = sequence_config(k)
+    name, seed, steps = args
+    cfg = sequence_config(name)
     rng = np.random.default_rng(seed)
     sc = make_sequence_scene(cfg, rng)
     out = []
@@ -436,14 +440,15 @@ def _sequence_chunk(args):
     return out
 
 
-def sequence_scans(k: int, n_scans: int | None = None, seed: int | None = None,
+def sequence_scans(name: str, n_scans: int | None = None, seed: int | None = None,
                    stride: int = 1, workers: int = 0):
-    """Scans 0, stride, 2*stride, ... of sequence configuration k (2 or 3).
+    """Scans 0, stride, 2*stride, ... of the sequence workload `name`
+    ("sequence" or "high_speed").
 
     workers > 1 casts the scans in a spawn-started process pool (each worker
     rebuilds the same seeded scene; the scans are identical)."""
-    cfg = sequence_config(k)
-    seed = SEED_BASE + k if seed is None else seed
+    cfg = sequence_config(name)
+    seed = SEEDS[name] if seed is None else seed
     n = cfg.n_scans if n_scans is None else n_scans
     steps = [i * stride for i in range(n)]
     if workers and workers > 1 and n > 1:
@@ -452,13 +457,13 @@ def sequence_scans(k: int, n_scans: int | None = None, seed: int | None = None,
         w = min(workers, n)
         chunks = [steps[i::w] for i in range(w)]
         with ProcessPoolExecutor(max_workers=w, mp_context=mp.get_context("spawn")) as ex:
-            parts = list(ex.map(_sequence_chunk, [(k, seed, c) for c in chunks]))
+            parts = list(ex.map(_sequence_chunk, [(name, seed, c) for c in chunks]))
         by_step = {}
         for c, part in zip(chunks, parts):
             for st, scan in zip(c, part):
                 by_step[st] = scan
         return cfg, [by_step[st] for st in steps]
-    return cfg, _sequence_chunk((k, seed, steps))
+    return cfg, _sequence_chunk((name, seed, steps))
 
 
 def _batched_map(args):
@@ -480,13 +485,14 @@ def _batched_map(args):
     return out
 
 
-def batched_scans(n_maps: int = 64, n_steps: int = 1, seed: int = SEED_BASE + 4,
+def batched_scans(n_maps: int = 64, n_steps: int = 1, seed: int | None = None,
                   lo: int = 8192, hi: int = 262144, workers: int = 0):
-    """Per step, a list of n_maps scans of log-uniform size (configuration 4).
+    """Per step, a list of n_maps scans of log-uniform size (the batched workload).
 
     workers > 1 generates maps in a spawn-started process pool (the result
     is the same as with one process)."""
     cfg = SequenceConfig(MapSpec(256, 256, 64, 0.2), LidarSpec(128, 2048, 22.5), n_steps, 4.5)
+    seed = SEEDS["batched"] if seed is None else seed
     jobs = [(seed, m, n_steps, lo, hi) for m in range(n_maps)]
     if workers and workers > 1:
         import multiprocessing as mp
@@ -523,13 +529,14 @@ def _served_robot(args):
 
 
 def served_requests(n_robots: int = 32, duration_s: float = 60.0, pool: int = 4,
-                    seed: int = SEED_BASE + 5, workers: int = 0):
-    """Robots (map spec, scan pool) and a time-ordered arrival list (configuration 5).
+                    seed: int | None = None, workers: int = 0):
+    """Robots (map spec, scan pool) and a time-ordered arrival list (the served workload).
 
     Returns (robots, arrivals): robots[i] = dict(map=MapSpec, lidar=LidarSpec,
     scans=[Scan]*pool); arrivals = list of (t_arrival_s, robot, pool_index).
     Robot i cycles through its pool of consecutive scans. workers > 1 builds
     robots in a spawn-started process pool (same result)."""
+    seed = SEEDS["served"] if seed is None else seed
     jobs = [(seed, i, pool) for i in range(n_robots)]
     if workers and workers > 1:
         import multiprocessing as mp
@@ -551,15 +558,14 @@ def served_requests(n_robots: int = 32, duration_s: float = 60.0, pool: int = 4,
     return robots, arr
 
 
-CONFIGS = {
-    1: dict(name="plain single scan: 16-beam, 16,384+2,000 pts, map 128x128x32 @ 0.2 m",
-            map=MapSpec(128, 128, 32, 0.2)),
-    2: dict(name="plain sequence: 64-beam, 131,072 pts/scan x 20 scans, map 256x256x64 @ 0.2 m, shift every scan",
-            map=MapSpec(256, 256, 64, 0.2)),
-    3: dict(name="plain high-speed: 128-beam, 262,144 pts/scan x 40 scans at 12 m/s, map 512x512x64 @ 0.1 m",
-            map=MapSpec(512, 512, 64, 0.1)),
-    4: dict(name="batched: 64 maps 256x256x64 @ 0.2 m, log-uniform 8,192-262,144 pts/scan",
-            map=MapSpec(256, 256, 64, 0.2)),
-    5: dict(name="served: 32 robots, 10 Hz Poisson arrivals, mixed sensors and maps",
-            map=None),
+WORKLOADS = {
+    "single_scan": dict(name="plain single scan: 16-beam, 16,384+2,000 pts, map 128x128x32 @ 0.2 m",
+                        map=MapSpec(128, 128, 32, 0.2)),
+    "sequence": dict(name="plain sequence: 64-beam, 131,072 pts/scan x 20 scans, map 256x256x64 @ 0.2 m, "
+                          "shift every scan", map=MapSpec(256, 256, 64, 0.2)),
+    "high_speed": dict(name="plain high-speed: 128-beam, 262,144 pts/scan x 40 scans at 12 m/s, "
+                            "map 512x512x64 @ 0.1 m", map=MapSpec(512, 512, 64, 0.1)),
+    "batched": dict(name="batched: 64 maps 256x256x64 @ 0.2 m, log-uniform 8,192-262,144 pts/scan",
+                    map=MapSpec(256, 256, 64, 0.2)),
+    "served": dict(name="served: 32 robots, 10 Hz Poisson arrivals, mixed sensors and maps", map=None),
 }

@@ -121,7 +121,7 @@ def test_batch_without_extraction_then_single_extract(gv):
 
 def test_batch_matches_oracle_on_sequence_scans(gv):
     # three maps of the 256 x 256 x 64 kind, scans from the sequence workload
-    cfg, scans = synth.sequence_scans(2, n_scans=3, stride=4)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=3, stride=4)
     ms = cfg.map
     params = oracle.OracleParams(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
     maps = [gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=params.neg_max_px) for _ in range(3)]

@@ -73,7 +73,7 @@ def rough_scan(rng, n, centre):
 
 def test_buffer_full_size_sequence(gv):
     # the 256 x 256 x 64 map, shifting every scan, buffer of 3 scans
-    cfg, scans = synth.sequence_scans(2, n_scans=6)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=6)
     params = oracle.OracleParams(nx=cfg.map.nx, ny=cfg.map.ny, nz=cfg.map.nz, res=cfg.map.res,
                                  neg_max_px=int(math.ceil(2.0 / cfg.map.res)))
     om = oracle.BufferedOracleMap(params, K=3)

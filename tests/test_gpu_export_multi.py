@@ -57,7 +57,7 @@ def compare_lut(gm, om, params):
 def test_lut_after_scans_and_shifts(gv):
     # the 256 x 256 x 64 map after shifting scans: the ring offset is not
     # zero, so the export walks logical order over toroidal storage
-    cfg, scans = synth.sequence_scans(2, n_scans=3)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=3)
     params = oracle.OracleParams(nx=cfg.map.nx, ny=cfg.map.ny, nz=cfg.map.nz, res=cfg.map.res,
                                  neg_max_px=int(math.ceil(2.0 / cfg.map.res)))
     om = oracle.OracleMap(params)

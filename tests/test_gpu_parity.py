@@ -101,34 +101,34 @@ def run_sequence(gv, params, scans, stride=3, check_each=True):
     return gm, om
 
 
-def test_config1_single_scan(gv):
-    s = synth.config1_scan()
-    params = params_for(synth.CONFIGS[1]["map"])
+def test_single_scan(gv):
+    s = synth.single_scan()
+    params = params_for(synth.WORKLOADS["single_scan"]["map"])
     gm, om = run_sequence(gv, params, [s])
     compare_stats(gm, om)
     out, ref = compare_products(gm, om)
     assert np.count_nonzero(out["flags"] & 2) > 0 and np.count_nonzero(out["flags"] & 8) > 0
 
 
-def test_config1_stride4(gv):
-    s = synth.config1_scan()
-    params = params_for(synth.CONFIGS[1]["map"])
+def test_single_scan_stride4(gv):
+    s = synth.single_scan()
+    params = params_for(synth.WORKLOADS["single_scan"]["map"])
     gm, om = run_sequence(gv, params, [s], stride=4)
     compare_products(gm, om)
 
 
-def test_config2_sequence_first_scans(gv):
+def test_sequence_first_scans(gv):
     # the 256 x 256 x 64 map, shifting every scan, at full size
-    cfg, scans = synth.sequence_scans(2, n_scans=4)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=4)
     params = params_for(cfg.map)
     gm, om = run_sequence(gv, params, scans)
     compare_stats(gm, om)
     compare_products(gm, om)
 
 
-def test_config3_scans_full_size(gv):
+def test_high_speed_scans_full_size(gv):
     # the 512 x 512 x 64 map at 0.1 m: two consecutive scans (12 voxels apart)
-    cfg, scans = synth.sequence_scans(3, n_scans=2, stride=1)
+    cfg, scans = synth.sequence_scans("high_speed", n_scans=2, stride=1)
     params = params_for(cfg.map)
     gm, om = run_sequence(gv, params, scans)
     compare_stats(gm, om)
@@ -200,7 +200,7 @@ def test_shift_sequences_match(gv):
 
 def test_accumulated_products_after_many_scans(gv):
     # a longer sequence on a small map: products after each of several scans
-    cfg, scans = synth.sequence_scans(2, n_scans=3, stride=5)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=3, stride=5)
     params = params_for(cfg.map, nx=96, ny=96, nz=32)
     om = oracle.OracleMap(params)
     gm = gv.VoxelMap(gpu_config(gv, params))

@@ -51,7 +51,7 @@ def run_both(gv, kw, scans, max_points):
 
 
 def test_pipeline_full_size_sequence(gv):
-    cfg, scans = synth.sequence_scans(2, n_scans=5)
+    cfg, scans = synth.sequence_scans("sequence", n_scans=5)
     ms = cfg.map
     kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
     seq = [dict(points=s.points, T_ws=s.T_ws, vehicle_xyz=s.vehicle_xyz) for s in scans]

@@ -223,11 +223,11 @@ def test_negative_threshold_is_strict_and_distance_bounded():
     assert not np.any(f2 & 8)
 
 
-# --- qualitative scene outcomes (config 1) ---------------------------------
+# --- qualitative scene outcomes (the single-scan test scene) ---------------
 @pytest.fixture(scope="module")
-def config1_maps():
+def single_scan_maps():
     import synth
-    s = synth.config1_scan()
+    s = synth.single_scan()
     params = oracle.OracleParams()
     m = oracle.OracleMap(params)
     m.shift_for_pose(s.vehicle_xyz)
@@ -239,8 +239,8 @@ def _px(m, x, y):
     return int(np.floor(x / m.params.res)) - m.origin[0], int(np.floor(y / m.params.res)) - m.origin[1]
 
 
-def test_scene_box_is_hard_obstacle(config1_maps):
-    m, out = config1_maps
+def test_scene_box_is_hard_obstacle(single_scan_maps):
+    m, out = single_scan_maps
     for bx, by in ((5.0, 3.0), (-4.0, -5.0)):
         ix, iy = _px(m, bx, by)
         win = out["flags"][ix - 4:ix + 5, iy - 4:iy + 5]
@@ -248,8 +248,8 @@ def test_scene_box_is_hard_obstacle(config1_maps):
         assert np.count_nonzero(win & 4) <= np.count_nonzero(win & 2)
 
 
-def test_scene_vegetation_is_soft(config1_maps):
-    m, out = config1_maps
+def test_scene_vegetation_is_soft(single_scan_maps):
+    m, out = single_scan_maps
     x0, y0 = _px(m, -6.0, 2.0)
     x1, y1 = _px(m, -3.0, 5.0)
     win = out["flags"][x0 + 1:x1 - 1, y0 + 1:y1 - 1]
@@ -257,11 +257,11 @@ def test_scene_vegetation_is_soft(config1_maps):
     assert np.count_nonzero(win & 2) < 0.1 * win.size
 
 
-def test_scene_ditch_is_negative(config1_maps):
+def test_scene_ditch_is_negative(single_scan_maps):
     # the ditch (x in [7, 9]) hides its floor and the ground just past its far
     # lip; the hidden pixels there see assumed heights that differ by more
     # than the threshold (Fig. 3, hole type)
-    m, out = config1_maps
+    m, out = single_scan_maps
     x0, y0 = _px(m, 7.0, -3.0)
     x1, y1 = _px(m, 10.6, 3.0)
     win = out["flags"][x0:x1, y0:y1]
@@ -276,8 +276,8 @@ def test_scene_ditch_is_negative(config1_maps):
     assert not np.any(out["flags"][gx - 2:gx + 3, gy - 2:gy + 3])
 
 
-def test_scene_ground_slope_is_five_degrees(config1_maps):
-    m, out = config1_maps
+def test_scene_ground_slope_is_five_degrees(single_scan_maps):
+    m, out = single_scan_maps
     x0, y0 = _px(m, 1.0, -3.0)
     x1, y1 = _px(m, 4.0, 0.0)
     s = out["slope"][x0:x1, y0:y1]

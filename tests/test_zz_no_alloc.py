@@ -56,10 +56,10 @@ def _noalloc_maps(gv, cfg, hits, passes, minz):
 
 def test_noalloc_matches_extract_maps_on_consecutive_calls(gv):
     # two different maps in a row: the second call reuses the fixed scratch
-    scans = [synth.config1_scan()]
-    cfg2, seq = synth.sequence_scans(2, n_scans=1)
+    scans = [synth.single_scan()]
+    cfg_seq, seq = synth.sequence_scans("sequence", n_scans=1)
     scans.append(seq[0])
-    specs = [synth.CONFIGS[1]["map"], cfg2.map]
+    specs = [synth.WORKLOADS["single_scan"]["map"], cfg_seq.map]
     for ms, s in zip(specs, scans):
         cfg = gv.make_config(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
         m = gv.VoxelMap(cfg)
