@@ -515,17 +515,13 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
         // Visit the current voxel, then take the next crossing group,
         // unless it moves the major axis past this segment. The ray's last
         // voxel (no crossings left) is the endpoint voxel: no pass.
+        // The step is branch-free: a lane that stops keeps stepping its
+        // (no longer read) state until the whole warp has stopped.
+        unsigned int item_n = 0;
         while (__any_sync(0xffffffffu, live)) {
-            uint32_t key = 0xffffffffu;
-            bool inside = false;
-            if (live) {
-                if (w.total == 0) {
-                    live = false;
-                } else {
-                    inside = (unsigned)w.cA < (unsigned)w.nA && (unsigned)w.cB < (unsigned)w.nB;
-                    if (inside) key = walk_index(w);
-                }
-            }
+            live = live && w.total != 0;
+            const bool inside = live && (unsigned)w.cA < (unsigned)w.nA && (unsigned)w.cB < (unsigned)w.nB;
+            const uint32_t key = inside ? walk_index(w) : 0xffffffffu;
             // runs of neighbouring lanes in the same voxel merge their
             // increments: the run's first lane adds the run's length
             bool boundary;
@@ -539,27 +535,20 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 boundary = lane == 0 || prev != key;
             }
             const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-            if (inside) {
-                if (boundary) {
-                    const unsigned int after = starts & ~((2u << lane) - 1u);
-                    const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
-                    atomicAdd(passes + key, run);
-                    if (kSlot && spasses) atomicAdd(spasses + key, run);
-                }
-                item_visits += 1;
+            if (inside && boundary) {
+                const unsigned int after = starts & ~((2u << lane) - 1u);
+                const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
+                atomicAdd(passes + key, run);
+                if (kSlot && spasses) atomicAdd(spasses + key, run);
             }
-            if (!live) continue;
+            item_n += inside ? 1u : 0u;
             const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
             const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
             const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
-            if (gM) {
-                if (w.segM == 0) {
-                    live = false;
-                    continue;
-                }
-                w.segM -= 1;
-                w.cM += w.dirM;
-            }
+            // the major step past the segment's last slab ends the segment
+            live = live && !(gM && w.segM == 0);
+            w.segM -= gM ? 1 : 0;
+            w.cM += gM ? w.dirM : 0;
             w.cA += gA ? w.dirA : 0;
             w.cB += gB ? w.dirB : 0;
             w.dMA += (gM ? w.sA : 0) - (gA ? w.sM : 0);
@@ -568,8 +557,9 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
             w.total -= (int)gM + (int)gA + (int)gB;
             // a minor axis past the window never comes back (steps are unit,
             // so it passes the window exactly at its exit voxel)
-            if (w.cA == w.exitA || w.cB == w.exitB) live = false;
+            live = live && w.cA != w.exitA && w.cB != w.exitB;
         }
+        item_visits = item_n;
         if (kBatch && __any_sync(0xffffffffu, own_item != own)) {
             flush_visits(a1, descs, own, visits);
             own = own_item;
