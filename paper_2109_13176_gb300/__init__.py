@@ -557,6 +557,25 @@ class VoxelMap:
                 "slope": torch.empty(n2, dtype=torch.float32, device=dev),
                 "roughness": torch.empty(n2, dtype=torch.float32, device=dev)}
 
+    def alloc_maps_packed(self, device=None, pin_memory=False):
+        """The five products as views into one contiguous byte buffer (each
+        product 256-byte aligned), so that one copy moves them all. Returns
+        (buffer, dict of views). On the CPU, pin_memory gives page-locked
+        memory."""
+        import torch
+        dev = device or torch.device("cuda")
+        nx, ny = self.cfg.nx, self.cfg.ny
+        layout = [("height", torch.float32, 4), ("density", torch.float32, 4), ("slope", torch.float32, 4),
+                  ("roughness", torch.float32, 4), ("flags", torch.uint8, 1)]
+        offs, o = [], 0
+        for _, _, sz in layout:
+            offs.append(o)
+            o += (nx * ny * sz + 255) // 256 * 256
+        buf = torch.empty(o, dtype=torch.uint8, device=dev, pin_memory=pin_memory and str(dev) == "cpu")
+        views = {name: buf[off:off + nx * ny * sz].view(dt).view(nx, ny)
+                 for (name, dt, sz), off in zip(layout, offs)}
+        return buf, views
+
     def extract_maps(self, out=None, stream=None):
         out = out if out is not None else self.alloc_maps()
         gvom_extract_maps(self.handle, out.get("height"), out.get("density"), out.get("flags"),

@@ -96,3 +96,28 @@ def test_pipeline_tickets_and_slots(gv):
         pipe.submit((0, 0, 0), torch.zeros((101, 3), dtype=torch.float32), T)  # beyond max_points
     pipe.close()
     m.close()
+
+
+def test_packed_products_equal_separate(gv):
+    # the products written into one packed buffer (one readback copy) equal
+    # the separately allocated ones
+    cfg, scans = synth.sequence_scans("sequence", n_scans=1)
+    ms = cfg.map
+    m = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    s = scans[0]
+    m.update(s.vehicle_xyz, torch.from_numpy(s.points).cuda(), s.T_ws)
+    ref = m.extract_maps()
+    buf, views = m.alloc_maps_packed()
+    m.extract_maps(views)
+    host = torch.empty(buf.numel(), dtype=torch.uint8, pin_memory=True)
+    host.copy_(buf)
+    _, hviews = m.alloc_maps_packed(device=torch.device("cpu"))
+    for k, v in ref.items():
+        np.testing.assert_array_equal(views[k].cpu().numpy(), v.cpu().numpy(), err_msg=k)
+    # the host copy holds the same bytes at the same offsets
+    off = 0
+    for k in ("height", "density", "slope", "roughness", "flags"):
+        n = ref[k].numel() * ref[k].element_size()
+        np.testing.assert_array_equal(host[off:off + n].numpy(), views[k].contiguous().view(torch.uint8).reshape(-1).cpu().numpy())
+        off += (n + 255) // 256 * 256
+    m.close()
