@@ -65,6 +65,18 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_over_ranks(times, counts, device):
+    """Replica aggregation: each time is the slowest rank's, each count the
+    sum over ranks (the whole job's work in the whole job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(times), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(v) for v in t], [float(v) for v in c]
+
+
 def gen_workers() -> int:
     return max(1, min(16, (os.cpu_count() or 2) - 1))
 
@@ -615,12 +627,7 @@ def main():
     e2e_s = sum(e2e_ms) * 1e-3
 
     if world > 1:
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        r = torch.tensor([rays, rays_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-        total_s, e2e_s = float(t[0]), float(t[1])
-        rays, rays_e2e = float(r[0]), float(r[1])
+        (total_s, e2e_s), (rays, rays_e2e) = reduce_over_ranks([total_s, e2e_s], [rays, rays_e2e], "cuda")
 
     if rank != 0:
         dist.destroy_process_group() if world > 1 else None
