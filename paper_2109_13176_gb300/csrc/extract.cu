@@ -437,13 +437,14 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
     }
 }
 
-constexpr int kMaxTile = 16;
+// Tile edge of the pixel pass for halo R: for R <= 12 the tile whose row
+// with both halos is one warp wide (tile + 2R = 32: each cone sweep step is
+// one instruction per lane, and no lane idles), else 16.
+__host__ __device__ __forceinline__ int tile_for_halo(int R) { return R <= 12 ? 32 - 2 * R : 16; }
 
-// Tile edge of the pixel pass: 8 for halos up to 12 pixels (more blocks,
-// one sweep step per lane), else 16 (less halo overhead).
 __host__ __device__ __forceinline__ int tile_edge(const ExtractParams& p) {
     const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
-    return R <= 12 ? 8 : kMaxTile;
+    return tile_for_halo(R);
 }
 constexpr int kPxBlock = 128;        // four warps: all fit planes, then each sweeps one cone direction
 
@@ -701,9 +702,20 @@ __global__ void __launch_bounds__(kPxBlock, 8) k_slope_negative_batch(BatchTable
 }
 
 size_t slope_negative_smem_halo(int R) {
-    const int tile = R <= 12 ? 8 : kMaxTile;
+    const int tile = tile_for_halo(R);
     const int W = tile + 2 * R;
     return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * tile * tile);
+}
+
+// Shared memory for any halo up to R (a batch holds maps of several halos;
+// a smaller halo can need more, for its larger tile).
+size_t slope_negative_smem_upto(int R) {
+    size_t m = 0;
+    for (int r = 1; r <= R; ++r) {
+        const size_t b = slope_negative_smem_halo(r);
+        m = b > m ? b : m;
+    }
+    return m;
 }
 
 size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_halo(tile_halo(p)); }
@@ -763,7 +775,7 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
     k_columns_batch<<<(unsigned)(sms * 8), kColBlock, 0, st>>>(t);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = slope_negative_smem_halo(max_halo);
+    const size_t smem = slope_negative_smem_upto(max_halo);
     if (smem > 48 * 1024) {
         static std::atomic<int> cache[64];
         e = allow_smem((const void*)k_slope_negative_batch, cache, smem);
