@@ -213,7 +213,8 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->s.minz, sizeof(float) * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->w.item_count, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&m->lut_counts, sizeof(unsigned int) * (size_t)gvom::lut_blocks(V));
     m->s.V = (uint32_t)V;
     const int K = cfg->scan_buffer;
@@ -286,6 +287,9 @@ int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
     for (int k = 0; k < 3; ++k) m->origin[k] = origin[k];
     m->buf_head = 0;
     m->buf_occupied = 0;
+    // the work list starts empty again (after an error mid-scan it may not be)
+    const cudaError_t e = cudaMemsetAsync(m->w.item_count, 0, 2 * sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(gvom::launch_init_state(m->s, voxels(m), (cudaStream_t)stream));
 }
 

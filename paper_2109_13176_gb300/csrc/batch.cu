@@ -181,7 +181,7 @@ int gvom_batch_create(int32_t max_maps, int64_t max_points, int32_t flags, gvom_
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tables[1], b->L.bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[1], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b->w.item_count, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->w.item_count, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&b->w.rays, sizeof(int4) * (size_t)max_points);
     if (e == cudaSuccess) b->w.cap_points = max_points;

@@ -134,9 +134,11 @@ __device__ __forceinline__ void column_scalar(const MapState& s, const ExtractPa
 __global__ void __launch_bounds__(kColBlock) k_columns_scalar(MapState s, ExtractParams p, float* __restrict__ height,
                                                                float* __restrict__ density,
                                                                uint8_t* __restrict__ flags) {
+    pdl_wait();
     const long long col = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
     if (col >= (long long)p.g.nx * p.g.ny) return;
     column_scalar(s, p, height, density, flags, col);
+    pdl_done();
 }
 
 // One step of the vector column pass for one warp: lane group lane / LPC
@@ -242,12 +244,14 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
 template <int LPC>
 __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams p, float* __restrict__ height,
                                                         float* __restrict__ density, uint8_t* __restrict__ flags) {
+    pdl_wait();
     const long long ncols = (long long)p.g.nx * p.g.ny;
     const long long groups_per_warp = 32 / LPC;
     const long long gw = ((long long)blockIdx.x * kColBlock + threadIdx.x) >> 5;
     const long long cstride = (((long long)gridDim.x * kColBlock) >> 5) * groups_per_warp;
     for (long long colb = gw * groups_per_warp; colb < ncols; colb += cstride)
         columns_step<LPC>(s, p, height, density, flags, colb, ncols);
+    pdl_done();
 }
 
 // ---- TMA-staged column pass (nz % 4 == 0) ----------------------------------
@@ -317,6 +321,7 @@ __device__ __forceinline__ void tma_issue(const MapState& s, int nz, long long n
 __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
                                                             float* __restrict__ density,
                                                             uint8_t* __restrict__ flags) {
+    pdl_wait();
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int s_fail;
     const Geom g = p.g;
@@ -435,6 +440,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
         }
         atomicOr(s.counters + kStatus, 1ull);
     }
+    pdl_done();
 }
 
 // Tile edge of the pixel pass for halo R: for R <= 12 the tile whose row
@@ -637,9 +643,11 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
 __global__ void __launch_bounds__(kPxBlock, 8)
     k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
                      float* __restrict__ rough, uint8_t* __restrict__ flags) {
+    pdl_wait();
     extern __shared__ float smem[];
     const int tile = tile_edge(p);
     tile_body(p, height, slope, rough, flags, blockIdx.y * tile, blockIdx.x * tile, tile, smem);
+    pdl_done();
 }
 
 // ---- batched maps ----------------------------------------------------------
@@ -806,14 +814,14 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
         long long blocks = (long long)sm_count() * per_sm;
         if (blocks > chunks) blocks = chunks;
         count_launch();
-        k_columns_tma<<<(unsigned)blocks, kTmaBlock, smem, st>>>(s, p, height, density, flags);
-        return cudaGetLastError();
+        return launch_pdl(k_columns_tma, dim3((unsigned)blocks), dim3(kTmaBlock), smem, st, s, p, height, density,
+                          flags);
     }
     count_launch();
     if ((p.g.nz & 3) != 0) {
         const long long blocks = (cols * 32 + kColBlock - 1) / kColBlock;
-        k_columns_scalar<<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
-        return cudaGetLastError();
+        return launch_pdl(k_columns_scalar, dim3((unsigned)blocks), dim3(kColBlock), 0, st, s, p, height, density,
+                          flags);
     }
     const int nv = p.g.nz / 4;
     const int lpc = nv <= 8 ? 8 : (nv <= 16 ? 16 : 32);
@@ -822,12 +830,10 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
     const long long cap = (long long)sm_count() * 8;
     if (blocks > cap) blocks = cap;
     if (lpc == 8)
-        k_columns<8><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
-    else if (lpc == 16)
-        k_columns<16><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
-    else
-        k_columns<32><<<(unsigned)blocks, kColBlock, 0, st>>>(s, p, height, density, flags);
-    return cudaGetLastError();
+        return launch_pdl(k_columns<8>, dim3((unsigned)blocks), dim3(kColBlock), 0, st, s, p, height, density, flags);
+    if (lpc == 16)
+        return launch_pdl(k_columns<16>, dim3((unsigned)blocks), dim3(kColBlock), 0, st, s, p, height, density, flags);
+    return launch_pdl(k_columns<32>, dim3((unsigned)blocks), dim3(kColBlock), 0, st, s, p, height, density, flags);
 }
 
 cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, float* slope, float* rough,
@@ -842,8 +848,7 @@ cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, f
     const int tile = tile_edge(p);
     dim3 grid((p.g.ny + tile - 1) / tile, (p.g.nx + tile - 1) / tile);
     count_launch();
-    k_slope_negative<<<grid, kPxBlock, smem, st>>>(p, height, slope, rough, flags);
-    return cudaGetLastError();
+    return launch_pdl(k_slope_negative, grid, dim3(kPxBlock), smem, st, p, height, slope, rough, flags);
 }
 
 cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,

@@ -10,6 +10,32 @@
 
 namespace gvom {
 
+// Programmatic dependent launch. The path's kernels are launched with
+// launch_pdl: a kernel waits until its predecessor's memory is visible
+// before touching it (pdl_wait, first thing), and lets its own successor
+// start launching once its block has done its main work (pdl_done), so the
+// successor's launch overlaps this kernel's tail rather than its body.
+// Launched without the attribute, both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_done() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Window geometry as the kernels see it. Voxel state is stored with
 // toroidal addressing: the world voxel W lives at physical slot
 // (W mod n) on every axis, so a window shift only rewrites the voxels that
@@ -46,7 +72,7 @@ enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3
 struct RayScratch {
     int4* rays;               // cap_points entries: (qx, qy, qz, nseg)
     uint2* items;             // cap_items entries: (point index, segment index)
-    unsigned long long* item_count; // one word
+    unsigned long long* item_count; // two words: the list's length, and blocks of the walk done with it
     long long cap_points;
     long long cap_items;
 };

@@ -621,12 +621,14 @@ __device__ __forceinline__ void evict_quad(const MapState& s, unsigned long long
 }
 
 __global__ void __launch_bounds__(256) k_evict(MapState s, unsigned long long mask) {
+    pdl_wait();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if ((s.V & 3u) == 0u) {
         if (4u * t < s.V) evict_quad(s, mask, 4u * t);
     } else if (t < s.V) {
         evict_voxel(s, mask, t);
     }
+    pdl_done();
 }
 
 // Fill the state with the empty voxel: no hits, no passes, min height +inf.
@@ -667,6 +669,7 @@ __device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
 }
 
 __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_xslab, long long n_units) {
+    pdl_wait();
     const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (u >= n_units) return;
@@ -684,9 +687,11 @@ __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_
     }
     const uint32_t base = column_base(g, cx, cy);
     for (int cz = lane; cz < g.nz; cz += 32) clear_voxel(s, base + (uint32_t)cz);
+    pdl_done();
 }
 
 __global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
+    pdl_wait();
     const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
     const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int wy = g.ny - ady;
@@ -700,6 +705,7 @@ __global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
         pz -= (pz >= g.nz) ? g.nz : 0;
         clear_voxel(s, base + (uint32_t)pz);
     }
+    pdl_done();
 }
 
 // ---- batched maps ----------------------------------------------------------
@@ -856,7 +862,7 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
-    cudaError_t e = cudaMemsetAsync(shared.w.item_count, 0, sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(shared.w.item_count, 0, 2 * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     long long sblocks = (long long)sms * 8;
     if (sblocks * 256 < max_maps) sblocks = (max_maps + 255) / 256;
@@ -905,8 +911,7 @@ cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_
     const long long threads = (s.V & 3u) == 0u ? (long long)s.V / 4 : (long long)s.V;
     const long long blocks = (threads + 255) / 256;
     count_launch();
-    k_evict<<<(unsigned)blocks, 256, 0, st>>>(s, mask);
-    return cudaGetLastError();
+    return launch_pdl(k_evict, dim3((unsigned)blocks), dim3(256), 0, st, s, mask);
 }
 
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st) {
@@ -918,8 +923,8 @@ cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d
         const int block = 256;
         const long long blocks = (n_cols * 32 + block - 1) / block;
         count_launch();
-        k_shift_columns<<<(unsigned)blocks, block, 0, st>>>(s, g_new, dx, dy, n_xslab, n_cols);
-        const cudaError_t e = cudaGetLastError();
+        const cudaError_t e =
+            launch_pdl(k_shift_columns, dim3((unsigned)blocks), dim3(block), 0, st, s, g_new, dx, dy, n_xslab, n_cols);
         if (e != cudaSuccess) return e;
     }
     if (adz > 0) {
@@ -927,8 +932,8 @@ cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d
         if (n > 0) {
             const int block = 256;
             count_launch();
-            k_shift_zslab<<<(unsigned)((n + block - 1) / block), block, 0, st>>>(s, g_new, dx, dy, dz);
-            return cudaGetLastError();
+            return launch_pdl(k_shift_zslab, dim3((unsigned)((n + block - 1) / block)), dim3(block), 0, st, s, g_new,
+                              dx, dy, dz);
         }
     }
     return cudaSuccess;
