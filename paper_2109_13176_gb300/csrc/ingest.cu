@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
     int qo[3];
     const bool sensor_ok = block_sensor(a, qo);
     rays_body(a, (long long)blockIdx.x * kRaysBlock, qo, sensor_ok, 0, 0u);
+    pdl_done();
 }
 
 // Phase 2: walk the segments.
@@ -468,6 +469,7 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
 
 template <bool kBatch, bool kSlot>
 __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const unsigned long long total_items = *a1.w.item_count;
     const long long n_items =
@@ -567,6 +569,7 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
         visits += item_visits;
     }
 
+    pdl_done();
     flush_visits(a1, descs, own, visits);
 }
 
@@ -949,11 +952,13 @@ cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStre
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
+    const IngestArgs* none = nullptr;
+    const int4* no_sensors = nullptr;
     if (a.slot >= 0)
-        k_march<false, true><<<march_grid<false, true>(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
-    else
-        k_march<false, false><<<march_grid<false, false>(shape), shape.block, 0, st>>>(a, nullptr, nullptr);
-    return cudaGetLastError();
+        return launch_pdl(k_march<false, true>, dim3(march_grid<false, true>(shape)), dim3(shape.block), 0, st, a,
+                          none, no_sensors);
+    return launch_pdl(k_march<false, false>, dim3(march_grid<false, false>(shape)), dim3(shape.block), 0, st, a, none,
+                      no_sensors);
 }
 
 }  // namespace gvom
