@@ -274,6 +274,7 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
 }
 
 __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
+    pdl_wait();
     int qo[3];
     const bool sensor_ok = block_sensor(a, qo);
     rays_body(a, (long long)blockIdx.x * kRaysBlock, qo, sensor_ok, 0, 0u);
@@ -571,6 +572,15 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
 
     pdl_done();
     flush_visits(a1, descs, own, visits);
+    if (!kBatch) {
+        // the last block to finish empties the work list for the next scan
+        // (every thread of every block read its length at the start)
+        __syncthreads();
+        if (threadIdx.x == 0 && atomicAdd(a1.w.item_count + 1, 1ull) + 1 == gridDim.x) {
+            a1.w.item_count[0] = 0;
+            a1.w.item_count[1] = 0;
+        }
+    }
 }
 
 // Empties the ring slots of `mask` at voxel i: their counts leave the
@@ -944,12 +954,10 @@ cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d
 
 cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(a.w.item_count, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
+    // the work list is empty here: the previous scan's walk emptied it
     const long long blocks = (a.n + kRaysBlock - 1) / kRaysBlock;
     count_launch();
-    k_rays<<<(unsigned)blocks, kRaysBlock, 0, st>>>(a);
-    e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_rays, dim3((unsigned)blocks), dim3(kRaysBlock), 0, st, a);
     if (e != cudaSuccess) return e;
     count_launch();
     const IngestArgs* none = nullptr;
