@@ -704,8 +704,7 @@ def main():
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         staging.copy_(hp, non_blocking=True)
-        gmap.update(s.vehicle_xyz, staging, s.T_ws)
-        gmap.extract_maps(packed_out)
+        gmap.update_extract(s.vehicle_xyz, staging, s.T_ws, packed_out)
         packed_host.copy_(packed_dev, non_blocking=True)
         e1.record(stream)
         e1.synchronize()

@@ -256,6 +256,13 @@ GVOM_API int gvom_extract_voxels(struct gvom_map* map, uint32_t* hits_dev, uint3
 GVOM_API int gvom_ingest_multi(struct gvom_map* map, int32_t k, const float* const* pts_dev, const int64_t* n,
                                int32_t stride, const double* T_ws, gvom_stream_t stream);
 
+/* One scan's whole update: gvom_update then gvom_extract_maps, in one call
+ * (Sec. III-C, III-D). Arguments, ownership and errors as those two calls;
+ * an invalid argument changes nothing. Stream-ordered. */
+GVOM_API int gvom_update_extract(struct gvom_map* map, const double vehicle_xyz[3], const float* pts_dev, int64_t n,
+                                 int32_t stride, const double T_ws[12], const gvom_maps_out* out,
+                                 gvom_stream_t stream);
+
 /* Exports the map in the paper's storage format (Sec. III-A): a lookup
  * table with one int64 entry per voxel, in logical (window) order, holding
  * the voxel's index in the data array if it is occupied (hits >= 1) and

@@ -122,6 +122,7 @@ def load_library():
             "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
             "gvom_ingest_multi": ([vp, i32, P(vp), P(i64), i32, P(ctypes.c_double), vp], ctypes.c_int),
+            "gvom_update_extract": ([vp, d3, vp, i64, i32, d3, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_export_lut": ([vp, vp, vp, vp, vp, i64, vp, vp], ctypes.c_int),
             "gvom_pipeline_create": ([vp, i64, P(vp)], ctypes.c_int),
             "gvom_pipeline_destroy": ([vp], None),
@@ -151,8 +152,9 @@ def _check(status: int, what: str) -> None:
 
 
 def _d(vals, n):
-    arr = (ctypes.c_double * n)(*[float(v) for v in vals])
-    return arr
+    import numpy as np
+    a = np.ascontiguousarray(vals, dtype=np.float64).reshape(n)
+    return (ctypes.c_double * n).from_buffer_copy(a)
 
 
 def _i64(vals):
@@ -162,7 +164,7 @@ def _i64(vals):
 def _T(T_ws):
     import numpy as np
     t = np.ascontiguousarray(T_ws, dtype=np.float64).reshape(12)
-    return (ctypes.c_double * 12)(*t.tolist())
+    return (ctypes.c_double * 12).from_buffer_copy(t)
 
 
 def _stream_handle(stream) -> int | None:
@@ -260,6 +262,16 @@ def gvom_update(handle: int, vehicle_xyz, points, T_ws, stream=None) -> None:
     ptr, n, stride = _points_args(points)
     _check(load_library().gvom_update(handle, _d(vehicle_xyz, 3), ptr, n, stride, _T(T_ws), _stream_handle(stream)),
            "gvom_update")
+
+
+def gvom_update_extract(handle: int, vehicle_xyz, points, T_ws, outs: dict, stream=None) -> None:
+    """Update with one scan (device points) and extract every product into
+    outs (dict of device tensors, see VoxelMap.alloc_maps), in one call."""
+    ptr, n, stride = _points_args(points)
+    o = gvom_maps_out(*(outs[k].data_ptr() if outs.get(k) is not None else None
+                        for k in ("height", "density", "flags", "slope", "roughness")))
+    _check(load_library().gvom_update_extract(handle, _d(vehicle_xyz, 3), ptr, n, stride, _T(T_ws), ctypes.byref(o),
+                                              _stream_handle(stream)), "gvom_update_extract")
 
 
 def gvom_extract_maps(handle: int, height=None, density=None, flags=None, slope=None, roughness=None,
@@ -590,6 +602,10 @@ class VoxelMap:
         minz = torch.empty(shp, dtype=torch.float32, device="cuda")
         gvom_extract_voxels(self.handle, hits, passes, minz, stream)
         return hits, passes, minz
+
+    def update_extract(self, vehicle_xyz, points, T_ws, out, stream=None):
+        gvom_update_extract(self.handle, vehicle_xyz, points, T_ws, out, stream)
+        return out
 
     def ingest_multi(self, points, T_ws, stream=None):
         gvom_ingest_multi(self.handle, points, T_ws, stream)

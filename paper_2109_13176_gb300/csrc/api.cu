@@ -375,6 +375,14 @@ int gvom_extract_maps(gvom_map* m, const gvom_maps_out* out, gvom_stream_t strea
     return cuda_status(e);
 }
 
+int gvom_update_extract(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, int64_t n, int32_t stride,
+                        const double T_ws[12], const gvom_maps_out* out, gvom_stream_t stream) {
+    if (!m || !out) return GVOM_ERR_INVALID_ARG;
+    const int rc = gvom_update(m, vehicle_xyz, pts_dev, n, stride, T_ws, stream);
+    if (rc != GVOM_OK) return rc;
+    return gvom_extract_maps(m, out, stream);
+}
+
 int gvom_extract_voxels(gvom_map* m, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
                         gvom_stream_t stream) {
     if (!m) return GVOM_ERR_INVALID_ARG;

@@ -81,6 +81,7 @@ def test_null_arguments_rejected(lib):
     assert lib.gvom_pipeline_wait(None, 1) == gv.GVOM_ERR_INVALID_ARG
     assert lib.gvom_pipeline_products(None, 1, None) == gv.GVOM_ERR_INVALID_ARG
     lib.gvom_pipeline_destroy(None)  # no-op
+    assert lib.gvom_update_extract(None, T, None, 0, 3, T, None, None) == gv.GVOM_ERR_INVALID_ARG
     lib.gvom_destroy(None)  # no-op
 
 

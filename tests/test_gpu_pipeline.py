@@ -121,3 +121,20 @@ def test_packed_products_equal_separate(gv):
         np.testing.assert_array_equal(host[off:off + n].numpy(), views[k].contiguous().view(torch.uint8).reshape(-1).cpu().numpy())
         off += (n + 255) // 256 * 256
     m.close()
+
+
+def test_update_extract_equals_separate_calls(gv):
+    cfg, scans = synth.sequence_scans("sequence", n_scans=2)
+    ms = cfg.map
+    kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    a, b = gv.VoxelMap(**kw), gv.VoxelMap(**kw)
+    _, views = a.alloc_maps_packed()
+    for s in scans:
+        p = torch.from_numpy(s.points).cuda()
+        a.update_extract(s.vehicle_xyz, p, s.T_ws, views)
+        b.update(s.vehicle_xyz, p, s.T_ws)
+    ref = b.extract_maps()
+    for k in ref:
+        np.testing.assert_array_equal(views[k].cpu().numpy(), ref[k].cpu().numpy(), err_msg=k)
+    a.close()
+    b.close()
