@@ -97,7 +97,7 @@ struct gvom_batch {
     // captured graph and what it was captured for
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
-    int g_B, g_extract, g_halo, g_slots;
+    int g_B, g_extract, g_halo, g_slots, g_zmax;
     long long g_cap_items;
     long long g_kernels;  // kernels in the captured graph, counted per replay
     long long steps;
@@ -233,6 +233,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     // validate everything before any state changes
     long long total = 0, items = 0;
     int halo = 0;
+    int zmax = 0;  // the largest nz, or -1 when some map cannot use the bulk-copy column pass
     for (int m = 0; m < B; ++m) {
         const gvom_map* mp = maps[m];
         if (!mp || n[m] < 0 || (n[m] > 0 && !pts_dev[m])) return GVOM_ERR_INVALID_ARG;
@@ -246,8 +247,11 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         items += n[m] * gvom::max_segments_per_ray(gvom::geom_of(mp), b->tune.seg_len);
         const int hm = gvom::tile_halo(gvom::extract_params(mp));
         halo = hm > halo ? hm : halo;
+        const int nz = mp->cfg.nz;
+        if (zmax >= 0) zmax = ((nz & 3) == 0 && nz <= 256) ? (nz > zmax ? nz : zmax) : -1;
     }
     if (total > b->max_points) return GVOM_ERR_INVALID_ARG;
+    if (zmax < 0) zmax = 0;
     int64_t* new_o = b->new_o;
     for (int m = 0; m < B; ++m) {
         const int rc = gvom_origin_for_pose(maps[m], vehicle_xyz + 3 * m, new_o + 3 * m);
@@ -348,12 +352,12 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
 
     if (!(b->flags & GVOM_BATCH_GRAPH)) {
         e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, st);
-        if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, halo, st);
+        if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, halo, zmax, st);
         return gvom::cuda_status(e);
     }
 
     if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items ||
-        b->g_slots != slots) {
+        b->g_slots != slots || b->g_zmax != zmax) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
         const long long before = gvom_kernel_launches();
@@ -361,7 +365,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         if (e == cudaSuccess) {
             cudaError_t le =
                 gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, b->cap_stream);
-            if (le == cudaSuccess && do_extract) le = gvom::launch_batch_extract(t, b->max_maps, halo, b->cap_stream);
+            if (le == cudaSuccess && do_extract)
+                le = gvom::launch_batch_extract(t, b->max_maps, halo, zmax, b->cap_stream);
             e = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e == cudaSuccess) e = le;
         }
@@ -374,6 +379,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         }
         b->g_extract = do_extract;
         b->g_halo = halo;
+        b->g_zmax = zmax;
         b->g_slots = slots;
         b->g_cap_items = b->w.cap_items;
         b->g_kernels = gvom_kernel_launches() - before;

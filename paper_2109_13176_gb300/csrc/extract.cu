@@ -306,35 +306,79 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 3 * kTmaCols * nz * sizeof(float); }
 
-// Starts the copies of chunk `chunk` into `stage`.
-__device__ __forceinline__ void tma_issue(const MapState& s, int nz, long long ncols, long long chunk, int stage,
-                                          unsigned long long* bars, uint32_t* hb, float* mb, uint32_t* pb) {
-    const long long c0 = chunk * kTmaCols;
+// One chunk of kTmaCols consecutive physical columns of one map.
+struct ChunkRef {
+    MapState s;
+    ExtractParams p;
+    float* height;
+    float* density;
+    uint8_t* flags;
+    long long lc;  // the chunk's index within its map
+};
+
+// The chunks of one map.
+struct OneMapChunks {
+    MapState s;
+    ExtractParams p;
+    float* height;
+    float* density;
+    uint8_t* flags;
+    __device__ __forceinline__ long long total() const {
+        return ((long long)p.g.nx * p.g.ny + kTmaCols - 1) / kTmaCols;
+    }
+    __device__ __forceinline__ ChunkRef at(long long c) const { return ChunkRef{s, p, height, density, flags, c}; }
+};
+
+// The chunks of every map of a batch step, map after map (col_prefix counts
+// kColTask = kTmaCols columns per unit).
+struct BatchChunks {
+    BatchTables t;
+    __device__ __forceinline__ long long total() const { return t.hdr->col_tasks; }
+    __device__ __forceinline__ ChunkRef at(long long c) const {
+        const int B = t.hdr->B;
+        int lo = 0, hi = B - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (t.col_prefix[mid] <= c)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchExtract& ex = t.ex[lo];
+        return ChunkRef{ex.s, ex.p, ex.height, ex.density, ex.flags, c - t.col_prefix[lo]};
+    }
+};
+
+// Starts the copies of chunk r into `stage` (stage buffers hold kTmaCols
+// columns of zmax voxels; the chunk's own columns are nz long).
+__device__ __forceinline__ void tma_issue(const ChunkRef& r, int zmax, int stage, unsigned long long* bars, uint32_t* hb,
+                                          float* mb, uint32_t* pb) {
+    const int nz = r.p.g.nz;
+    const long long ncols = (long long)r.p.g.nx * r.p.g.ny;
+    const long long c0 = r.lc * kTmaCols;
     const long long cols = ncols - c0 < kTmaCols ? ncols - c0 : kTmaCols;
     const unsigned bytes = (unsigned)(cols * nz * 4);
+    const size_t so = (size_t)stage * kTmaCols * zmax;
     mbar_expect_tx(&bars[stage], 3u * bytes);
-    bulk_load(hb + (size_t)stage * kTmaCols * nz, s.hits + c0 * nz, bytes, &bars[stage]);
-    bulk_load(mb + (size_t)stage * kTmaCols * nz, s.minz + c0 * nz, bytes, &bars[stage]);
-    bulk_load(pb + (size_t)stage * kTmaCols * nz, s.passes + c0 * nz, bytes, &bars[stage]);
+    bulk_load(hb + so, r.s.hits + c0 * nz, bytes, &bars[stage]);
+    bulk_load(mb + so, r.s.minz + c0 * nz, bytes, &bars[stage]);
+    bulk_load(pb + so, r.s.passes + c0 * nz, bytes, &bars[stage]);
 }
 
-__global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
-                                                            float* __restrict__ density,
-                                                            uint8_t* __restrict__ flags) {
-    pdl_wait();
+// The bulk-copy column pass over the chunks of `src` (a persistent grid;
+// every map's nz is a multiple of 4 and at most zmax <= 256). A wait that
+// gives up sets the status word of the map whose chunk it waited for.
+template <typename Src>
+__device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int s_fail;
-    const Geom g = p.g;
-    const int nz = g.nz, nv = nz >> 2;
-    const long long ncols = (long long)g.nx * g.ny;
-    const long long nchunks = (ncols + kTmaCols - 1) / kTmaCols;
+    const long long nchunks = src.total();
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm);
     uint32_t* hb = reinterpret_cast<uint32_t*>(sm + 128);
-    float* mb = reinterpret_cast<float*>(hb + (size_t)kTmaStages * kTmaCols * nz);
-    uint32_t* pb = reinterpret_cast<uint32_t*>(mb + (size_t)kTmaStages * kTmaCols * nz);
+    float* mb = reinterpret_cast<float*>(hb + (size_t)kTmaStages * kTmaCols * zmax);
+    uint32_t* pb = reinterpret_cast<uint32_t*>(mb + (size_t)kTmaStages * kTmaCols * zmax);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int sub = lane & 7;                      // lane within the column's 8-lane group
-    const Band band = make_band(p.obs_min_h, p.obs_max_h);
 
     if (tid == 0) {
         for (int st = 0; st < kTmaStages; ++st) mbar_init(&bars[st], 1);
@@ -345,7 +389,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
     if (tid == 0)
         for (int st = 0; st < kTmaStages; ++st) {
             const long long c = blockIdx.x + (long long)st * gridDim.x;
-            if (c < nchunks) tma_issue(s, nz, ncols, c, st, bars, hb, mb, pb);
+            if (c < nchunks) tma_issue(src.at(c), zmax, st, bars, hb, mb, pb);
         }
 
     int k = 0;
@@ -356,10 +400,17 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
         if (!mbar_wait(&bars[st], (unsigned)((k / kTmaStages) & 1))) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
-        const uint32_t* hst = hb + (size_t)st * kTmaCols * nz;
-        const float* mst = mb + (size_t)st * kTmaCols * nz;
-        const uint32_t* pst = pb + (size_t)st * kTmaCols * nz;
-        const long long c0 = c * kTmaCols;
+        const ChunkRef r = src.at(c);
+        const ExtractParams& p = r.p;
+        const Geom g = p.g;
+        const int nz = g.nz, nv = nz >> 2;
+        const long long ncols = (long long)g.nx * g.ny;
+        const Band band = make_band(p.obs_min_h, p.obs_max_h);
+        const size_t so = (size_t)st * kTmaCols * zmax;
+        const uint32_t* hst = hb + so;
+        const float* mst = mb + so;
+        const uint32_t* pst = pb + so;
+        const long long c0 = r.lc * kTmaCols;
         // 8 warps x 4 columns = the chunk's 32 columns
         const int j = warp * 4 + (lane >> 3);
         const long long pc = c0 + j;                 // physical column
@@ -414,7 +465,7 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
             int cy = py - g.ry;
             cy += cy < 0 ? g.ny : 0;
             const size_t o = (size_t)cx * g.ny + cy;
-            if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
+            if (r.height) r.height[o] = col_any ? h : __int_as_float(0x7fffffff);
             uint8_t f = 0;
             float dens = 0.0f;
             if (H > 0) {
@@ -422,13 +473,13 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
                 const bool hard = H * (unsigned long long)p.hard_den >= (unsigned long long)p.hard_num * (H + M);
                 f = hard ? 3 : 5;
             }
-            if (density) density[o] = dens;
-            if (flags) flags[o] = f;
+            if (r.density) r.density[o] = dens;
+            if (r.flags) r.flags[o] = f;
         }
         __syncthreads();  // every warp is done with this stage
         if (tid == 0) {
             const long long c2 = c + (long long)kTmaStages * gridDim.x;
-            if (c2 < nchunks) tma_issue(s, nz, ncols, c2, st, bars, hb, mb, pb);
+            if (c2 < nchunks) tma_issue(src.at(c2), zmax, st, bars, hb, mb, pb);
         }
     }
     if (s_fail && tid == 0) {
@@ -438,9 +489,20 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractPa
             if (c >= nchunks) break;
             mbar_wait(&bars[q % kTmaStages], (unsigned)((q / kTmaStages) & 1));
         }
-        atomicOr(s.counters + kStatus, 1ull);
+        atomicOr(src.at(blockIdx.x + (long long)k * gridDim.x).s.counters + kStatus, 1ull);
     }
+}
+
+__global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
+                                                            float* __restrict__ density,
+                                                            uint8_t* __restrict__ flags) {
+    pdl_wait();
+    columns_tma_body(OneMapChunks{s, p, height, density, flags}, p.g.nz);
     pdl_done();
+}
+
+__global__ void __launch_bounds__(kTmaBlock) k_columns_tma_batch(BatchTables t, int zmax) {
+    columns_tma_body(BatchChunks{t}, zmax);
 }
 
 // Tile edge of the pixel pass for halo R: for R <= 12 the tile whose row
@@ -776,12 +838,32 @@ long long tiles_of(const ExtractParams& p) {
     return (long long)((p.g.nx + t - 1) / t) * ((p.g.ny + t - 1) / t);
 }
 
-cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st) {
+// Blocks per SM of the bulk-copy column pass: as many as shared memory
+// holds at once (1 KB of each block's share is reserved), at most 4.
+long long columns_tma_blocks_per_sm(size_t smem) {
+    int dev = 0, smem_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    long long per_sm = (long long)smem_sm / (long long)(smem + 1024);
+    if (per_sm > 4) per_sm = 4;
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, int zmax, cudaStream_t st) {
     (void)max_maps;
     const int sms = sm_count();
+    cudaError_t e;
     count_launch();
-    k_columns_batch<<<(unsigned)(sms * 8), kColBlock, 0, st>>>(t);
-    cudaError_t e = cudaGetLastError();
+    if (zmax > 0) {
+        const size_t smem = columns_tma_smem(zmax);
+        static std::atomic<int> cache[64];
+        e = allow_smem((const void*)k_columns_tma_batch, cache, smem);
+        if (e != cudaSuccess) return e;
+        k_columns_tma_batch<<<(unsigned)(sms * columns_tma_blocks_per_sm(smem)), kTmaBlock, smem, st>>>(t, zmax);
+    } else {
+        k_columns_batch<<<(unsigned)(sms * 8), kColBlock, 0, st>>>(t);
+    }
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = slope_negative_smem_upto(max_halo);
     if (smem > 48 * 1024) {
@@ -803,15 +885,7 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
         cudaError_t e = allow_smem((const void*)k_columns_tma, cache, smem);
         if (e != cudaSuccess) return e;
         const long long chunks = (cols + kTmaCols - 1) / kTmaCols;
-        // persistent grid: only as many blocks per SM as its shared memory
-        // holds at once (1 KB of each block's share is reserved)
-        int dev = 0, smem_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        long long per_sm = (long long)smem_sm / (long long)(smem + 1024);
-        if (per_sm > 4) per_sm = 4;
-        if (per_sm < 1) per_sm = 1;
-        long long blocks = (long long)sm_count() * per_sm;
+        long long blocks = (long long)sm_count() * columns_tma_blocks_per_sm(smem);
         if (blocks > chunks) blocks = chunks;
         count_launch();
         return launch_pdl(k_columns_tma, dim3((unsigned)blocks), dim3(kTmaBlock), smem, st, s, p, height, density,

@@ -159,7 +159,7 @@ struct BatchTables {
     long long* evict_prefix;  // [max_maps + 1], in 1024-voxel units
 };
 
-constexpr int kColTask = 64;       // columns per warp task of the batched column pass
+constexpr int kColTask = 32;       // columns per unit of the batched column pass (a bulk-copy chunk)
 long long shift_units(const Geom& g, const int d[3], int whole);
 long long tiles_of(const ExtractParams& p);
 int tile_halo(const ExtractParams& p);
@@ -168,7 +168,9 @@ int tile_halo(const ExtractParams& p);
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
                                 const MarchShape& shape, bool evict, bool slots, cudaStream_t st);
 long long evict_units(const MapState& s);
-cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, cudaStream_t st);
+// zmax > 0: every map's nz is a multiple of 4 and at most 256, zmax the
+// largest (the bulk-copy column pass); 0: the vector/scalar column pass.
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, int zmax, cudaStream_t st);
 
 // Lookup-table export (export.cu): blocks of the count / write kernels and
 // the three launches (count, scan, write).
