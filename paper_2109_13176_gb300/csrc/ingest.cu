@@ -800,8 +800,8 @@ __global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
     }
 }
 
-// Per-point pass of all maps: a persistent grid over the maps' 256-point
-// blocks; every block belongs to one map.
+// Per-point pass of all maps over the maps' 256-point blocks (one thread
+// block each, or fewer looping over them); every block belongs to one map.
 __global__ void __launch_bounds__(kRaysBlock) k_rays_batch(BatchTables t) {
     __shared__ int s_m;
     const int B = t.hdr->B;
@@ -887,8 +887,11 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
         k_evict_batch<<<(unsigned)(sms * 8), 256, 0, st>>>(t);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    long long rblocks = (long long)sms * 8;
-    if (rblocks > max_ray_blocks) rblocks = max_ray_blocks > 0 ? max_ray_blocks : 1;
+    // one block per 256-point block of the largest step the tables allow
+    // (blocks past this step's count return at once), so the hardware
+    // scheduler balances them
+    long long rblocks = max_ray_blocks > 0 ? max_ray_blocks : 1;
+    if (rblocks > 0x7fffffffLL) rblocks = 0x7fffffffLL;
     count_launch();
     k_rays_batch<<<(unsigned)rblocks, kRaysBlock, 0, st>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
