@@ -780,7 +780,9 @@ def main():
                              "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
         "cpu_baseline": cpu,
         "e2e": {"value": rays_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "ms_per_step_p50": statistics.median(e2e_ms),
+                "ms_per_step_p99": sorted(e2e_ms)[int(0.99 * (len(e2e_ms) - 1))],
+                "call": "pinned H2D copy, gvom_update_extract, one D2H copy of the packed products, per step"},
         "gpu_launches": int(launches),
         "clocks": clocks.summary(),
         "tuning": {"seg_len": tuning[0], "march_block": tuning[1], "march_blocks_per_sm": tuning[2],
