@@ -696,7 +696,8 @@ def main():
     d2h = packed_dev.numel()
     staging = torch.empty_like(dev_pts[0])
     e2e_ms = []
-    for i in range(args.steps):
+    e2e_steps = max(args.steps, 200)  # host-sensitive: a longer window
+    for i in range(e2e_steps):
         flush_buf.fill_(i & 0xff)
         k = args.warmup + args.steps + i
         s = scans[k % len(scans)]

@@ -299,17 +299,22 @@ def gvom_ingest_multi(handle: int, points, T_ws, stream=None) -> None:
     k = len(points)
     if k != len(T_ws) or k < 1:
         raise ValueError("one pose per scan, at least one scan")
-    strides = {int(p.shape[1]) for p in points}
-    if len(strides) != 1:
-        raise ValueError("all scans must have the same stride")
-    for p in points:
-        if p.dtype.is_floating_point is False or p.element_size() != 4 or not p.is_contiguous():
+    stride = int(points[0].shape[1])
+    ptrs = (ctypes.c_void_p * k)()
+    ns = (ctypes.c_int64 * k)()
+    for j, p in enumerate(points):
+        if p.dim() != 2 or int(p.shape[1]) != stride:
+            raise ValueError("all scans must be (n, 3) or all (n, 4)")
+        if p.element_size() != 4 or not p.dtype.is_floating_point or not p.is_contiguous():
             raise ValueError("points must be contiguous float32")
-    ptrs = (ctypes.c_void_p * k)(*[p.data_ptr() if p.shape[0] else None for p in points])
-    ns = (ctypes.c_int64 * k)(*[int(p.shape[0]) for p in points])
-    T = np.ascontiguousarray(np.stack([np.asarray(t, dtype=np.float64).reshape(12) for t in T_ws]))
-    Tc = (ctypes.c_double * (12 * k))(*T.reshape(-1).tolist())
-    _check(load_library().gvom_ingest_multi(handle, k, ptrs, ns, strides.pop(), Tc, _stream_handle(stream)),
+        n = int(p.shape[0])
+        ptrs[j] = p.data_ptr() if n else None
+        ns[j] = n
+    T = np.empty((k, 12), dtype=np.float64)
+    for j, t in enumerate(T_ws):
+        T[j] = np.asarray(t, dtype=np.float64).reshape(12)
+    Tc = (ctypes.c_double * (12 * k)).from_buffer_copy(T)
+    _check(load_library().gvom_ingest_multi(handle, k, ptrs, ns, stride, Tc, _stream_handle(stream)),
            "gvom_ingest_multi")
 
 

@@ -743,6 +743,11 @@ __device__ __forceinline__ int find_map(const long long* __restrict__ prefix, in
 __global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
     const int B = t.hdr->B;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        // the step's segment work list starts empty (all entries share it)
+        t.ing[0].w.item_count[0] = 0;
+        t.ing[0].w.item_count[1] = 0;
+    }
     if (tid < B) {
         const IngestArgs& a = t.ing[tid];
         int q[3];
@@ -875,8 +880,7 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
-    cudaError_t e = cudaMemsetAsync(shared.w.item_count, 0, 2 * sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     long long sblocks = (long long)sms * 8;
     if (sblocks * 256 < max_maps) sblocks = (max_maps + 255) / 256;
     count_launch();
