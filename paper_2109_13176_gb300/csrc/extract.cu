@@ -514,7 +514,8 @@ __host__ __device__ __forceinline__ int tile_edge(const ExtractParams& p) {
     const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
     return tile_for_halo(R);
 }
-constexpr int kPxBlock = 128;        // four warps: all fit planes, then each sweeps one cone direction
+constexpr int kPxBlock = 256;        // eight warps: four sweep one cone direction each, four fit planes
+constexpr int kPxBlockBatch = 128;   // the batched form: four warps, fits then cones (more blocks per SM)
 
 // Cone state of a cell, packed into one 64-bit key: the distance D of the
 // first ring holding ground in the high word, the lowest height on that ring
@@ -633,9 +634,10 @@ __device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* H
     ro = sse / (float)n;
 }
 
-// One tile of tile x tile pixels per block of four warps: load the tile and
-// its halo, fit the planes of the defined pixels, then warp w sweeps cone w
-// (+x, -x, +y, -y), and every pixel combines its four cone values.
+// One tile of tile x tile pixels per block of four or eight warps: load the
+// tile and its halo; warp w < 4 sweeps cone w (+x, -x, +y, -y) and the
+// planes of the defined pixels are fitted (by warps 4-7 at the same time,
+// or by all warps first); then every pixel combines its four cone values.
 __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* __restrict__ height,
                                           float* __restrict__ slope, float* __restrict__ rough,
                                           uint8_t* __restrict__ flags, int tx0, int ty0, int tile, float* smem) {
@@ -658,28 +660,35 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     }
     __syncthreads();
 
-    for (int t = threadIdx.x; t < tt; t += blockDim.x) {
-        const int li = t / tile, lj = t % tile;
-        const int cx = tx0 + li, cy = ty0 + lj;
-        if (cx >= nx || cy >= ny) continue;
-        const int ci = li + R, cj = lj + R;
-        const float h0 = Hs[ci * W + cj];
-        float sl = qnan, ro = qnan;
-        if (!isnan(h0)) {
-            if (r == 2)
-                plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
-            else if (r == 1)
-                plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
-            else
-                plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
+    // with eight warps, warps 0-3 sweep the four cones while warps 4-7 fit
+    // the planes; with four, all fit, then each sweeps one cone
+    const bool split = flags && blockDim.x >= 256;
+    const int fit0 = split ? 128 : 0;
+    if (!split || warp >= 4) {
+        for (int t = (int)threadIdx.x - fit0; t < tt; t += (int)blockDim.x - fit0) {
+            const int li = t / tile, lj = t % tile;
+            const int cx = tx0 + li, cy = ty0 + lj;
+            if (cx >= nx || cy >= ny) continue;
+            const int ci = li + R, cj = lj + R;
+            const float h0 = Hs[ci * W + cj];
+            float sl = qnan, ro = qnan;
+            if (!isnan(h0)) {
+                if (r == 2)
+                    plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
+                else if (r == 1)
+                    plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
+                else
+                    plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
+            }
+            const size_t o = (size_t)cx * ny + cy;
+            if (slope) slope[o] = sl;
+            if (rough) rough[o] = ro;
         }
-        const size_t o = (size_t)cx * ny + cy;
-        if (slope) slope[o] = sl;
-        if (rough) rough[o] = ro;
     }
     if (flags) {
-        cone_sweep_warp(p, Hs, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
-                        vals + warp * tt);
+        if (warp < 4)
+            cone_sweep_warp(p, Hs, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
+                            vals + warp * tt);
         __syncthreads();
         for (int t = threadIdx.x; t < tt; t += blockDim.x) {
             const int li = t / tile, lj = t % tile;
@@ -702,7 +711,7 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     __syncthreads();  // the caller may reuse the shared arrays for its next tile
 }
 
-__global__ void __launch_bounds__(kPxBlock, 8)
+__global__ void __launch_bounds__(kPxBlock, 4)
     k_slope_negative(ExtractParams p, const float* __restrict__ height, float* __restrict__ slope,
                      float* __restrict__ rough, uint8_t* __restrict__ flags) {
     pdl_wait();
@@ -756,7 +765,7 @@ __global__ void __launch_bounds__(kColBlock) k_columns_batch(BatchTables t) {
 }
 
 // Plane-fit / cone pass of all maps: a persistent grid over pixel tiles.
-__global__ void __launch_bounds__(kPxBlock, 8) k_slope_negative_batch(BatchTables t) {
+__global__ void __launch_bounds__(kPxBlockBatch, 8) k_slope_negative_batch(BatchTables t) {
     extern __shared__ float smem[];
     const int B = t.hdr->B;
     const long long total = t.hdr->tiles;
@@ -872,7 +881,7 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
         if (e != cudaSuccess) return e;
     }
     count_launch();
-    k_slope_negative_batch<<<(unsigned)(sms * 8), kPxBlock, smem, st>>>(t);
+    k_slope_negative_batch<<<(unsigned)(sms * 8), kPxBlockBatch, smem, st>>>(t);
     return cudaGetLastError();
 }
 
