@@ -17,7 +17,8 @@
  *  - Every function returns a gvom_status (0 on success). Arguments are
  *    checked before anything is enqueued, so a call that fails with
  *    GVOM_ERR_INVALID_ARG leaves the map unchanged. GVOM_ERR_CUDA reports a
- *    CUDA error seen while enqueueing; the map's state is then undefined.
+ *    CUDA error seen while enqueueing; the map's state is then undefined
+ *    until gvom_reset, which returns it to an empty, defined state.
  *  - Invalid points are not errors: non-finite points, points at range 0 or
  *    beyond max_range, and points too far from the window to quantise are
  *    dropped and counted in gvom_stats.
@@ -181,7 +182,8 @@ GVOM_API int gvom_origin_for_pose(const struct gvom_map* map, const double vehic
 /* Current window origin (world voxel of window voxel (0,0,0)). Host-only. */
 GVOM_API int gvom_get_origin(const struct gvom_map* map, int64_t out_origin[3]);
 
-/* Empties the map and places it at `origin`. Stream-ordered. */
+/* Empties the map (and its scan buffer) and places it at `origin`; also
+ * the way back to a defined state after GVOM_ERR_CUDA. Stream-ordered. */
 GVOM_API int gvom_reset(struct gvom_map* map, const int64_t origin[3], gvom_stream_t stream);
 
 /* Moves the window to new_origin (Sec. III-D combination by index offset):
