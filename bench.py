@@ -499,15 +499,18 @@ def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush,
         torch.cuda.synchronize()
         r0 = mp.stats()["rays_valid"]
         l0 = gv.gvom_kernel_launches()
-        ts = []
+        # like the main leg: events around each step, one synchronisation at
+        # the end (the host enqueues ahead of the device)
+        evs = []
         for i in range(n_steps):
             flush()
             e0, e1 = ev(), ev()
             e0.record(stream)
             fn(args.warmup + i)
             e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1))
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ts = [a.elapsed_time(b) for a, b in evs]
         return ((mp.stats()["rays_valid"] - r0) / (sum(ts) * 1e-3), statistics.median(ts),
                 (gv.gvom_kernel_launches() - l0) / n_steps)
 
