@@ -388,15 +388,16 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
         torch.cuda.synchronize()
         st0 = [m.stats()["rays_valid"] for m in maps]
         l0 = gv.gvom_kernel_launches()
-        ms_ = []
+        evs = []
         for k in range(args.batched_steps):
             flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn(args.warmup + k)
             e1.record(stream)
-            e1.synchronize()
-            ms_.append(e0.elapsed_time(e1))
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        ms_ = [a.elapsed_time(b) for a, b in evs]
         launches = (gv.gvom_kernel_launches() - l0) / args.batched_steps
         rays = sum(m.stats()["rays_valid"] for m in maps) - sum(st0)
         return rays / (sum(ms_) * 1e-3), statistics.median(ms_), launches, rays / args.batched_steps
