@@ -70,7 +70,6 @@ __device__ __forceinline__ unsigned int block_exclusive(unsigned int v, unsigned
 
 __global__ void __launch_bounds__(kLutBlock) k_lut_count(MapState s, Geom g, long long V, unsigned int* counts) {
     __shared__ unsigned int warp_sums[kLutBlock / 32];
-    __shared__ unsigned int total;
     const long long i0 = (long long)blockIdx.x * kLutSpan + (long long)threadIdx.x * kLutPer;
     unsigned int c = 0;
     if (i0 < V) {
@@ -80,41 +79,56 @@ __global__ void __launch_bounds__(kLutBlock) k_lut_count(MapState s, Geom g, lon
         for (int k = 0; k < kLutPer; ++k)
             if (i0 + k < V) c += s.hits[k_[k]] != 0u ? 1u : 0u;
     }
-    block_exclusive(c, warp_sums, &total);
-    if (threadIdx.x == 0) counts[blockIdx.x] = total;
+    // the block's total only (a reduction, not a scan)
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned int t = threadIdx.x < kLutBlock / 32 ? warp_sums[threadIdx.x] : 0u;
+        t = __reduce_add_sync(0xffffffffu, t);
+        if (threadIdx.x == 0) counts[blockIdx.x] = t;
+    }
 }
 
-// One block scans all block counts in place (exclusive) and writes the total.
+// One block scans all block counts in place (exclusive) and writes the
+// total: 4,096 counts per pass, four per thread (prefixes fit 32 bits, V < 2^31).
 __global__ void __launch_bounds__(1024) k_lut_scan(unsigned int* counts, long long nblocks, long long* n_occupied) {
-    __shared__ unsigned long long warp_sums[32];
-    __shared__ unsigned long long carry;
+    __shared__ unsigned int warp_sums[32];
+    __shared__ unsigned int carry;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (long long base = 0; base < nblocks; base += 1024) {
-        const long long i = base + threadIdx.x;
-        const unsigned long long v = i < nblocks ? counts[i] : 0ull;
-        unsigned long long x = v;  // inclusive scan within the warp
+    for (long long base = 0; base < nblocks; base += 4096) {
+        const long long i = base + 4 * (long long)threadIdx.x;
+        unsigned int v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = i + k < nblocks ? counts[i + k] : 0u;
+        const unsigned int t = v[0] + v[1] + v[2] + v[3];
+        unsigned int x = t;  // inclusive scan of the thread totals within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_sums[warp] = x;
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned long long sum = 0;
+            unsigned int sum = 0;
             for (int w = 0; w < 32; ++w) {
-                const unsigned long long t = warp_sums[w];
+                const unsigned int u = warp_sums[w];
                 warp_sums[w] = sum;
-                sum += t;
+                sum += u;
             }
         }
         __syncthreads();
-        const unsigned long long excl = carry + warp_sums[warp] + x - v;
-        if (i < nblocks) counts[i] = (unsigned int)excl;  // prefixes fit 32 bits: V < 2^31
-        __syncthreads();                                  // every thread has read carry
-        if (threadIdx.x == 1023) carry = excl + v;        // the tile's end
+        unsigned int excl = carry + warp_sums[warp] + x - t;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i + k < nblocks) counts[i + k] = excl;
+            excl += v[k];
+        }
+        __syncthreads();                             // every thread has read carry
+        if (threadIdx.x == 1023) carry = excl;       // the pass's end
         __syncthreads();
     }
     if (threadIdx.x == 0) *n_occupied = (long long)carry;

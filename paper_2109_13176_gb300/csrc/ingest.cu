@@ -620,6 +620,40 @@ __device__ __forceinline__ void evict_voxel(const MapState& s, unsigned long lon
 // load per array and slot finds the common case, four voxels that no
 // emptied slot touched.
 __device__ __forceinline__ void evict_quad(const MapState& s, unsigned long long mask, uint32_t i) {
+    if ((mask & (mask - 1ull)) == 0ull) {
+        // one slot (every scan of the plain and batched paths): the counts of
+        // the four voxels leave the map with 16-byte loads and stores
+        const int j = __ffsll((long long)mask) - 1;
+        const size_t o = (size_t)j * s.V + i;
+        uint4* sh = reinterpret_cast<uint4*>(s.ring_hits + o);
+        uint4* sp = reinterpret_cast<uint4*>(s.ring_passes + o);
+        const uint4 h = *sh, p = *sp;
+        if ((h.x | h.y | h.z | h.w | p.x | p.y | p.z | p.w) == 0u) return;
+        uint4* mh = reinterpret_cast<uint4*>(s.hits + i);
+        uint4* mp = reinterpret_cast<uint4*>(s.passes + i);
+        uint4 ah = *mh, ap = *mp;
+        ah.x -= h.x; ah.y -= h.y; ah.z -= h.z; ah.w -= h.w;
+        ap.x -= p.x; ap.y -= p.y; ap.z -= p.z; ap.w -= p.w;
+        *mh = ah;
+        *mp = ap;
+        *sh = make_uint4(0u, 0u, 0u, 0u);
+        *sp = make_uint4(0u, 0u, 0u, 0u);
+        if ((h.x | h.y | h.z | h.w) == 0u) return;
+        const uint32_t hs[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (hs[e] == 0u) continue;
+            const float mz = s.ring_minz[o + e];
+            s.ring_minz[o + e] = __int_as_float(0x7f800000);
+            if (mz == s.minz[i + e]) {
+                float m = __int_as_float(0x7f800000);
+                for (int k = 0; k < s.ring_K; ++k)
+                    if (k != j) m = fminf(m, s.ring_minz[(size_t)k * s.V + i + e]);
+                s.minz[i + e] = m;
+            }
+        }
+        return;
+    }
     uint32_t any = 0u;
     for (int j = 0; j < s.ring_K; ++j) {
         if (!((mask >> j) & 1ull)) continue;

@@ -92,6 +92,25 @@ def test_lut_ragged_windows(gv, dims):
     gm.close()
 
 
+def test_lut_several_scan_passes(gv):
+    # 8.4 M voxels: 8,192 block counts, two passes of the count scan
+    rng = np.random.default_rng(5)
+    params = oracle.OracleParams(nx=512, ny=512, nz=32, res=0.1)
+    om = oracle.OracleMap(params)
+    gm = gv.VoxelMap(gpu_config(gv, params))
+    o = (-256, -256, -16)
+    om.shift_to(o)
+    gm.shift(o)
+    for k in range(2):
+        pts = rng.normal(scale=[8.0, 8.0, 0.5], size=(20000, 3)).astype(np.float32)
+        T = np.array([[1.0, 0, 0, 0.3 * k], [0, 1.0, 0, -0.2 * k], [0, 0, 1.0, 0.8]])
+        om.ingest(pts, T)
+        gm.ingest(to_dev(pts), T)
+    table, data = compare_lut(gm, om, params)
+    assert len(data["hits"]) > 10000
+    gm.close()
+
+
 def test_lut_capacity_smaller_than_occupied(gv):
     rng = np.random.default_rng(3)
     params = oracle.OracleParams(nx=48, ny=40, nz=24, res=0.2)
