@@ -134,8 +134,8 @@ void or_shift(const or_params* p, const int64_t old_o[3], const int64_t new_o[3]
 }
 
 /* ---------------------------------------------------------------------- */
-/* Ray traversal (Sec. III-A "rays passing through the voxel", Sec. III-C
- * "the lidar rays are traced").
+/* Ray traversal (Sec. III-A: a voxel counts the rays that cross it;
+ * Sec. III-C: every lidar ray is traced).
  *
  * Endpoints are integers in 1/256-voxel units relative to the window origin.
  * The segment P(t) = A + t (B - A), t in [0, 1], meets cell c iff for some t
