@@ -9,6 +9,11 @@ ingest the scan (transform, hits, exact traversal passes), and extract every
 2D product (height, obstacles, density, slope, roughness, negative
 obstacles). Steps cycle through the 20 scans.
 
+Also measured (key "high_speed"): the high-speed workload -- a 128-beam
+lidar (262,144 points per scan) at 12 m/s into a 512 x 512 x 64 map at
+0.1 m, whose 201 MB of counts exceed L2. --workload high_speed makes it the
+main leg instead (both arms).
+
 Metric: rays integrated per second (valid rays / GPU time), with map updates
 per second beside it. The L2 is flushed (a 256 MiB write) between timed
 steps; each step is timed with CUDA events on the stream that runs it.
@@ -38,6 +43,7 @@ if ROOT not in sys.path:
 METRIC = "rays integrated/s (plain sequence map update: shift + ingest + extract)"
 UNIT = "rays/s"
 WORKLOAD = "plain sequence: 64-beam 64x2048 = 131,072 pts/scan, 20 scans at 10 Hz, 4.5 m/s, map 256x256x64 @ 0.2 m, shift every scan"
+METRIC_HIGH_SPEED = "rays integrated/s (plain high-speed map update: shift + ingest + extract)"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -56,6 +62,10 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--served-seconds", type=float, default=20.0, help="length of the replayed arrival stream")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
+    ap.add_argument("--no-high-speed", action="store_true", help="skip the 512x512x64 high-speed leg")
+    ap.add_argument("--high-speed-scans", type=int, default=8, help="generated scans of the high-speed leg")
+    ap.add_argument("--workload", choices=["sequence", "high_speed"], default="sequence",
+                    help="workload of the main leg (high_speed also drops the separate high-speed leg)")
     return ap.parse_args()
 
 
@@ -82,7 +92,9 @@ def gen_workers() -> int:
     return max(1, min(16, (os.cpu_count() or 2) - 1))
 
 
-def make_inputs(rank: int):
+def make_inputs(rank: int, workload: str = "sequence", n_scans: int = 8):
+    if workload == "high_speed":
+        return make_high_speed_inputs(rank, n_scans)
     import synth
     seed = synth.SEEDS["sequence"] + 1000 * rank
     cfg, scans = synth.sequence_scans("sequence", seed=seed, workers=gen_workers())
@@ -102,6 +114,16 @@ def make_served_inputs(rank: int, seconds: float):
     import synth
     return synth.served_requests(n_robots=32, duration_s=seconds, pool=4, seed=synth.SEEDS["served"] + 1000 * rank,
                                  workers=gen_workers())
+
+
+HIGH_SPEED_WORKLOAD = ("plain high-speed: 128-beam 128x2048 = 262,144 pts/scan at 10 Hz, 12 m/s, map 512x512x64 @ 0.1 m "
+                       "(201 MB of counts, larger than L2), shift every scan; {n} generated scans cycled")
+
+
+def make_high_speed_inputs(rank: int, n_scans: int):
+    import synth
+    return synth.sequence_scans("high_speed", n_scans=n_scans, seed=synth.SEEDS["high_speed"] + 1000 * rank,
+                                workers=gen_workers())
 
 
 def make_batched_inputs(rank: int, n_maps: int):
@@ -327,17 +349,19 @@ def profile_traffic(kernel: str, workload: str):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    cfg, scans = make_inputs(0)
+    hs = args.workload == "high_speed"
+    cfg, scans = make_inputs(0, args.workload, args.high_speed_scans)
     res = run_oracle_steps(cfg, scans, args.warmup + args.steps)
     timed = res[args.warmup:]
     rays = sum(r for r, _ in timed)
     secs = sum(t for _, t in timed)
     v = rays / secs
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC_HIGH_SPEED if hs else METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded procedural terrain and lidar model)",
-            "config": {"workload": WORKLOAD, "map": [cfg.map.nx, cfg.map.ny, cfg.map.nz], "res_m": cfg.map.res,
+            "config": {"workload": HIGH_SPEED_WORKLOAD.format(n=len(scans)) if hs else WORKLOAD,
+                       "map": [cfg.map.nx, cfg.map.ny, cfg.map.nz], "res_m": cfg.map.res,
                        "points_per_scan": cfg.lidar.n, "scans": len(scans)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{len(timed)} full scans of the workload (shift + ingest + extract each)"},
@@ -559,6 +583,82 @@ def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush,
     return out
 
 
+def run_high_speed(args, gv, tune, torch, inputs, flush, stream, hbm_peak):
+    """The high-speed workload on one map of 512 x 512 x 64 at 0.1 m: the
+    same timed step as the main leg (shift + ingest + extract, events per
+    step, L2 flushed between steps). Its state (201 MB of counts) does not
+    fit in L2, so the walk's atomics and the column pass meet HBM."""
+    cfg, scans = inputs
+    ms = cfg.map
+    dev = [torch.from_numpy(s.points).cuda() for s in scans]
+    m = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    o = m.alloc_maps()
+    nt = min(4, len(scans))
+    tuning, _ = tune.tune_map(m, dev[:nt], [s.T_ws for s in scans[:nt]], [s.vehicle_xyz for s in scans[:nt]],
+                              flush=flush, refresh=args.retune)
+    m.reset((0, 0, 0))
+    m.reset_stats()
+    ns = len(scans)
+
+    def step(k, e_ing=None):
+        s = scans[k % ns]
+        m.shift(m.origin_for_pose(s.vehicle_xyz))
+        m.ingest(dev[k % ns], s.T_ws)
+        if e_ing is not None:
+            e_ing.record(stream)
+        m.extract_maps(o)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    st0 = m.stats()
+    l0 = gv.gvom_kernel_launches()
+    evs = []
+    for i in range(args.steps):
+        flush()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        step(args.warmup + i, e[1])
+        e[2].record(stream)
+        evs.append(e)
+    torch.cuda.synchronize()
+    st1 = m.stats()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    upd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    ext_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    tot = sum(step_ms) * 1e-3
+    rays = st1["rays_valid"] - st0["rays_valid"]
+    visits = st1["pass_visits"] - st0["pass_visits"]
+    hits = st1["hits_in_window"] - st0["hits_in_window"]
+    V = ms.nx * ms.ny * ms.nz
+    ext_bytes = 12 * V + 17 * ms.nx * ms.ny
+    ext_s = statistics.mean(ext_ms) * 1e-3
+    out = {"workload": HIGH_SPEED_WORKLOAD.format(n=ns), "value": rays / tot, "unit": UNIT,
+           "map_updates_per_s": args.steps / tot, "ms_per_step_mean": 1e3 * tot / args.steps,
+           "ms_per_step_median": statistics.median(step_ms), "rays_per_step": rays / args.steps,
+           "pass_visits_per_step": visits / args.steps, "hits_per_step": hits / args.steps,
+           "shift_ingest_ms_mean": statistics.mean(upd_ms), "extract_ms_mean": 1e3 * ext_s,
+           "ingest_atomics": {"per_step": (visits + 2 * hits) / args.steps,
+                              "achieved_g_per_s": (visits + 2 * hits) / (sum(upd_ms) * 1e-3) / 1e9,
+                              "note": "pass visits + 2 per in-window hit over shift + ingest time"},
+           "extract_hbm": {"algorithmic_bytes": ext_bytes, "achieved_gbs": ext_bytes / ext_s / 1e9,
+                           "frac": ext_bytes / ext_s / 1e9 / hbm_peak if hbm_peak else None,
+                           "bytes_rule": "12 B/voxel read + 17 B/px written"},
+           "gpu_launches_per_step": (gv.gvom_kernel_launches() - l0) / args.steps,
+           "tuning": {"seg_len": tuning[0], "march_block": tuning[1], "march_blocks_per_sm": tuning[2]},
+           "l2": "flushed between timed steps (256 MiB write)"}
+    m.close()
+    return out
+
+
+def oracle_high_speed_baseline(inputs, time_budget_s: float):
+    """The oracle on the first scans of the high-speed workload (one thread)."""
+    cfg, scans = inputs
+    res = run_oracle_steps(cfg, scans, len(scans), time_budget_s=time_budget_s)
+    return {"value": sum(r for r, _ in res) / sum(t for _, t in res), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {len(res)} scans of the high-speed workload, shift + ingest + extract each, single thread"}
+
+
 def run_served(args, gv, torch, inputs):
     """The served workload: real-time replay with continuous batching (latency),
     then all requests at once (capacity), batched vs one plain update per scan."""
@@ -616,9 +716,13 @@ def main():
         return
 
     # inputs first: the generator's process pool starts before any CUDA call
-    cfg, scans = make_inputs(rank)
+    cfg, scans = make_inputs(rank, args.workload, args.high_speed_scans)
+    hs_main = args.workload == "high_speed"
+    metric = METRIC_HIGH_SPEED if hs_main else METRIC
+    workload = HIGH_SPEED_WORKLOAD.format(n=len(scans)) if hs_main else WORKLOAD
     batched_inputs = None if args.no_batched else make_batched_inputs(rank, args.batched_maps)
     served_inputs = None if args.no_served else make_served_inputs(rank, args.served_seconds)
+    hs_inputs = None if (args.no_high_speed or hs_main) else make_high_speed_inputs(rank, args.high_speed_scans)
 
     import numpy as np
     import torch
@@ -742,6 +846,11 @@ def main():
     if not args.no_next_rows:
         next_rows = run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush, stream,
                                   rays_e2e / e2e_s, peaks.get("hbm_gbs"))
+    high_speed = None
+    if hs_inputs is not None:
+        high_speed = run_high_speed(args, gv, tune, torch, hs_inputs, flush, stream, peaks.get("hbm_gbs"))
+        if not args.no_cpu_baseline:
+            high_speed["cpu_baseline"] = oracle_high_speed_baseline(hs_inputs, 6.0)
     red_peak = measure_red_peak(gv, torch)
     ingest_avg_s = statistics.mean(ingest_ms) * 1e-3
     atom_per_launch = (visits + 2 * hits) / args.steps
@@ -759,11 +868,11 @@ def main():
                "sample": f"first {len(res)} scans of the workload, shift + ingest + extract each, single thread"}
 
     line = {
-        "metric": METRIC, "value": rays / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": rays / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 transform, int32 traversal, u32 counts, f32 maps",
-        "data": "synthetic (seeded procedural terrain, boxes, ditches; 64-beam lidar model)",
-        "config": {"workload": WORKLOAD, "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
+        "data": f"synthetic (seeded procedural terrain, boxes, ditches; {cfg.lidar.beams}-beam lidar model)",
+        "config": {"workload": workload, "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
                    "points_per_scan": cfg.lidar.n, "scans": len(scans),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (one map per GPU)"},
@@ -774,7 +883,7 @@ def main():
                     "ingest_avg": 1e3 * ingest_avg_s, "extract_avg": 1e3 * extract_avg_s},
         "roofline": {"kernel": "k_ingest", "bound": "l2_atomic", "achieved": achieved / 1e9,
                      "peak": red_peak / 1e9, "unit": "Gatomic/s", "frac": achieved / red_peak,
-                     "traffic": profile_traffic("k_ingest", "plain_sequence"),
+                     "traffic": profile_traffic("k_ingest", "plain_high_speed" if hs_main else "plain_sequence"),
                      "peak_source": "measured in this run: scattered 32-bit reduction atomics over 64 MiB (gvom_microbench_red)",
                      "algorithmic": "pass visits + 2 atomics per in-window hit, per launch"},
         "roofline_step": roofline_step(atom_per_launch, red_peak, V, ms, cfg.lidar.n, peaks.get("hbm_gbs"),
@@ -795,6 +904,7 @@ def main():
         "batched": batched,
         "served": served,
         "next_rows": next_rows,
+        "high_speed": high_speed,
     }
     print(json.dumps(line), flush=True)
     gmap.close()
