@@ -65,3 +65,26 @@ def test_reference_arm_skips_other_ranks(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2)
     bench.run_reference(args, rank=1, world=2)   # returns at once, prints nothing
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys, monkeypatch):
+    # rank 0 prints one JSON line with the keys the benchmark contract names,
+    # its e2e and cpu_baseline describing the oracle run itself
+    import json
+
+    import bench
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"])
+    args = bench.parse()
+    bench.run_reference(args, rank=0, world=1)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 1 and line["value"] > 0
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["map"] == [256, 256, 64]
