@@ -97,7 +97,8 @@ struct gvom_batch {
     // captured graph and what it was captured for
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
-    int g_B, g_extract, g_halo, g_slots, g_zmax;
+    int g_B, g_extract, g_slots, g_zmax;
+    size_t g_px_smem;  // the captured pixel pass's shared memory per block
     long long g_cap_items;
     long long g_kernels;  // kernels in the captured graph, counted per replay
     long long steps;
@@ -232,7 +233,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     const cudaStream_t st = (cudaStream_t)stream;
     // validate everything before any state changes
     long long total = 0, items = 0;
-    int halo = 0;
+    size_t px_smem = 0;  // the pixel pass's shared memory: the largest any map of the step needs
     int zmax = 0;  // the largest nz, or -1 when some map cannot use the bulk-copy column pass
     for (int m = 0; m < B; ++m) {
         const gvom_map* mp = maps[m];
@@ -245,8 +246,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
             if (maps[j] == mp) return GVOM_ERR_INVALID_ARG;  // one update per map per step
         total += n[m];
         items += n[m] * gvom::max_segments_per_ray(gvom::geom_of(mp), b->tune.seg_len);
-        const int hm = gvom::tile_halo(gvom::extract_params(mp));
-        halo = hm > halo ? hm : halo;
+        const size_t pm = gvom::slope_negative_smem(gvom::extract_params(mp));
+        px_smem = pm > px_smem ? pm : px_smem;
         const int nz = mp->cfg.nz;
         if (zmax >= 0) zmax = ((nz & 3) == 0 && nz <= 256) ? (nz > zmax ? nz : zmax) : -1;
     }
@@ -352,11 +353,11 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
 
     if (!(b->flags & GVOM_BATCH_GRAPH)) {
         e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, st);
-        if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, halo, zmax, st);
+        if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, px_smem, zmax, st);
         return gvom::cuda_status(e);
     }
 
-    if (!b->exec || b->g_extract != do_extract || b->g_halo < halo || b->g_cap_items != b->w.cap_items ||
+    if (!b->exec || b->g_extract != do_extract || b->g_px_smem < px_smem || b->g_cap_items != b->w.cap_items ||
         b->g_slots != slots || b->g_zmax != zmax) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
@@ -366,7 +367,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
             cudaError_t le =
                 gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, b->cap_stream);
             if (le == cudaSuccess && do_extract)
-                le = gvom::launch_batch_extract(t, b->max_maps, halo, zmax, b->cap_stream);
+                le = gvom::launch_batch_extract(t, b->max_maps, px_smem, zmax, b->cap_stream);
             e = cudaStreamEndCapture(b->cap_stream, &graph);
             if (e == cudaSuccess) e = le;
         }
@@ -378,7 +379,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
             return gvom::cuda_status(e);
         }
         b->g_extract = do_extract;
-        b->g_halo = halo;
+        b->g_px_smem = px_smem;
         b->g_zmax = zmax;
         b->g_slots = slots;
         b->g_cap_items = b->w.cap_items;

@@ -508,11 +508,25 @@ __global__ void __launch_bounds__(kTmaBlock) k_columns_tma_batch(BatchTables t, 
 // Tile edge of the pixel pass for halo R: for R <= 12 the tile whose row
 // with both halos is one warp wide (tile + 2R = 32: each cone sweep step is
 // one instruction per lane, and no lane idles), else 16.
-__host__ __device__ __forceinline__ int tile_for_halo(int R) { return R <= 12 ? 32 - 2 * R : 16; }
+// Tile edge of the pixel pass for halo R on an nx x ny map. While R <= 12 a
+// tile row plus both halos is one warp wide (32 - 2R). For 12 < R <= 24 it is
+// two warps wide (64 - 2R) if the map still has kWideTilesMin such tiles
+// (two per SM): a wider tile halves the cone sweep's halo work per pixel.
+// Otherwise, and beyond 24, the edge is 16.
+constexpr long long kWideTilesMin = 2 * 152;
+
+__host__ __device__ __forceinline__ int tile_for(int R, int nx, int ny) {
+    if (R <= 12) return 32 - 2 * R;
+    if (R <= 24) {
+        const int t = 64 - 2 * R;
+        if ((long long)((nx + t - 1) / t) * ((ny + t - 1) / t) >= kWideTilesMin) return t;
+    }
+    return 16;
+}
 
 __host__ __device__ __forceinline__ int tile_edge(const ExtractParams& p) {
     const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
-    return tile_for_halo(R);
+    return tile_for(R, p.g.nx, p.g.ny);
 }
 constexpr int kPxBlock = 256;        // eight warps: four sweep one cone direction each, four fit planes
 constexpr int kPxBlockBatch = 128;   // the batched form: four warps, fits then cones (more blocks per SM)
@@ -780,24 +794,11 @@ __global__ void __launch_bounds__(kPxBlockBatch, 8) k_slope_negative_batch(Batch
     }
 }
 
-size_t slope_negative_smem_halo(int R) {
-    const int tile = tile_for_halo(R);
+size_t slope_negative_smem_tile(int R, int tile) {
     const int W = tile + 2 * R;
     return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * tile * tile);
 }
 
-// Shared memory for any halo up to R (a batch holds maps of several halos;
-// a smaller halo can need more, for its larger tile).
-size_t slope_negative_smem_upto(int R) {
-    size_t m = 0;
-    for (int r = 1; r <= R; ++r) {
-        const size_t b = slope_negative_smem_halo(r);
-        m = b > m ? b : m;
-    }
-    return m;
-}
-
-size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_halo(tile_halo(p)); }
 
 __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits, uint32_t* __restrict__ passes,
                                 float* __restrict__ minz) {
@@ -829,6 +830,8 @@ int sm_count() {
 
 }  // namespace
 
+size_t slope_negative_smem(const ExtractParams& p) { return slope_negative_smem_tile(tile_halo(p), tile_edge(p)); }
+
 cudaError_t allow_smem(const void* kernel, std::atomic<int>* cache, size_t bytes) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -858,7 +861,7 @@ long long columns_tma_blocks_per_sm(size_t smem) {
     return per_sm < 1 ? 1 : per_sm;
 }
 
-cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, int zmax, cudaStream_t st) {
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, size_t px_smem, int zmax, cudaStream_t st) {
     (void)max_maps;
     const int sms = sm_count();
     cudaError_t e;
@@ -874,7 +877,7 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_hal
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t smem = slope_negative_smem_upto(max_halo);
+    const size_t smem = px_smem;
     if (smem > 48 * 1024) {
         static std::atomic<int> cache[64];
         e = allow_smem((const void*)k_slope_negative_batch, cache, smem);

@@ -170,7 +170,10 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
 long long evict_units(const MapState& s);
 // zmax > 0: every map's nz is a multiple of 4 and at most 256, zmax the
 // largest (the bulk-copy column pass); 0: the vector/scalar column pass.
-cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, int max_halo, int zmax, cudaStream_t st);
+// px_smem: the pixel pass's shared memory per block, the largest
+// slope_negative_smem of the step's maps.
+cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, size_t px_smem, int zmax, cudaStream_t st);
+size_t slope_negative_smem(const ExtractParams& p);
 
 // Lookup-table export (export.cu): blocks of the count / write kernels and
 // the three launches (count, scan, write).

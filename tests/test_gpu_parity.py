@@ -260,3 +260,43 @@ def test_points_at_the_range_limit(gv):
     compare_voxels(gm, om)
     compare_stats(gm, om)
     assert 0 < om.stats.rays_valid < len(pts)
+
+
+def holes_and_blocks(rng, nx, ny, res, n):
+    """Ground points over the whole window with round holes (undefined
+    pixels) and raised blocks, so that the cone search meets ground of
+    several heights at several distances."""
+    ex, ey = nx * res, ny * res
+    x = rng.uniform(-ex / 2, ex / 2, n)
+    y = rng.uniform(-ey / 2, ey / 2, n)
+    z = 0.25 * np.sin(x / 3.0) + 0.2 * np.cos(y / 4.0) + rng.normal(0, 0.02, n)
+    keep = np.ones(n, bool)
+    for _ in range(max(4, int(ex * ey / 45))):
+        cx, cy, r = rng.uniform(-ex / 2, ex / 2), rng.uniform(-ey / 2, ey / 2), rng.uniform(0.3, 2.6)
+        keep &= (x - cx) ** 2 + (y - cy) ** 2 > r * r
+    for _ in range(max(3, int(ex * ey / 70))):
+        cx, cy = rng.uniform(-ex / 2, ex / 2), rng.uniform(-ey / 2, ey / 2)
+        m = (np.abs(x - cx) < rng.uniform(0.5, 2)) & (np.abs(y - cy) < rng.uniform(0.5, 2))
+        z[m] += rng.uniform(0.2, 0.6)
+    return np.stack([x[keep], y[keep], z[keep]], 1).astype(np.float32)
+
+
+@pytest.mark.parametrize("nx,ny,halo", [(430, 410, 20), (200, 180, 13), (160, 150, 30)])
+def test_pixel_tiles_for_large_search_distances(gv, nx, ny, halo):
+    # search distances above 12 px: two-warp-wide tiles when the map has
+    # enough of them (430 x 410, 20 px: 24-px tiles, ragged on both axes),
+    # else 16-px tiles (a small map at 13 px; 30 px)
+    rng = np.random.default_rng(halo)
+    params = oracle.OracleParams(nx=nx, ny=ny, nz=16, res=0.1, neg_max_px=halo)
+    o = (-(nx // 2), -(ny // 2), -8)
+    om = oracle.OracleMap(params, o)
+    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm.shift(o)
+    pts = holes_and_blocks(rng, nx, ny, 0.1, int(1.1 * nx * ny))
+    pts[:, 2] -= 20.0                     # sensor frame: the sensor 20 m above the ground
+    T = np.array([[1.0, 0, 0, 0.0], [0, 1.0, 0, 0.0], [0, 0, 1.0, 20.0]])
+    om.ingest(pts, T)
+    gm.ingest(to_dev(pts), T)
+    compare_voxels(gm, om)
+    out, ref = compare_products(gm, om)
+    assert (ref["flags"] & 8).any() and np.isfinite(ref["slope"]).sum() > nx * ny // 5
