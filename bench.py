@@ -92,6 +92,23 @@ def gen_workers() -> int:
     return max(1, min(16, (os.cpu_count() or 2) - 1))
 
 
+def host_cpu() -> dict:
+    """The host the CPU baselines ran on: logical CPUs and the CPU model."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key, _, val = line.partition(":")
+                fields.setdefault(key.strip(), val.strip())
+    except OSError:
+        pass
+    import platform
+    model = fields.get("model name") or fields.get("Model") or ""
+    if not model and "CPU part" in fields:  # Arm: implementer and part numbers
+        model = f"{platform.machine()} (implementer {fields.get('CPU implementer', '?')}, part {fields['CPU part']})"
+    return {"nproc": os.cpu_count() or 0, "model": model or platform.machine()}
+
+
 def make_inputs(rank: int, workload: str = "sequence", n_scans: int = 8):
     if workload == "high_speed":
         return make_high_speed_inputs(rank, n_scans)
@@ -200,7 +217,7 @@ def oracle_batched_baseline(inputs, n_maps: int):
         res = list(ex.map(_oracle_map_job, jobs))
     wall = time.perf_counter() - t0
     rays = sum(r for r, _ in res)
-    return {"value": rays / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": rays / wall, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host_cpu(),
             "sample": f"first step of the first {len(jobs)} maps, one map per process (spawned), wall time "
                       "including process start"}
 
@@ -227,7 +244,7 @@ def oracle_served_baseline(inputs, time_budget_s: float):
         n += 1
         if time.perf_counter() - t_all > time_budget_s:
             break
-    return {"value": rays / sum(per), "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": rays / sum(per), "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"first {n} requests in arrival order, each robot's own map, one thread",
             "mean_ms_per_request": 1e3 * statistics.fmean(per)}
 
@@ -363,7 +380,7 @@ def run_reference(args, rank, world):
             "config": {"workload": HIGH_SPEED_WORKLOAD.format(n=len(scans)) if hs else WORKLOAD,
                        "map": [cfg.map.nx, cfg.map.ny, cfg.map.nz], "res_m": cfg.map.res,
                        "points_per_scan": cfg.lidar.n, "scans": len(scans)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{len(timed)} full scans of the workload (shift + ingest + extract each)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "map_updates_per_s": len(timed) / secs}
@@ -656,6 +673,7 @@ def oracle_high_speed_baseline(inputs, time_budget_s: float):
     cfg, scans = inputs
     res = run_oracle_steps(cfg, scans, len(scans), time_budget_s=time_budget_s)
     return {"value": sum(r for r, _ in res) / sum(t for _, t in res), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"first {len(res)} scans of the high-speed workload, shift + ingest + extract each, single thread"}
 
 
@@ -864,7 +882,7 @@ def main():
         res = run_oracle_steps(cfg, scans, len(scans) * 10, time_budget_s=args.cpu_sample_s)
         cr = sum(r for r, _ in res)
         cs = sum(t for _, t in res)
-        cpu = {"value": cr / cs, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": cr / cs, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"first {len(res)} scans of the workload, shift + ingest + extract each, single thread"}
 
     line = {
