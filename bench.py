@@ -690,11 +690,22 @@ def run_served(args, gv, torch, inputs):
     def server():
         return Server(specs, slots=2, max_batch_maps=len(robots), max_batch_points=max_pts, reserve_bytes=2 << 30)
 
+    # the collector stays off during each replay, as in the main leg's timed region
     srv = server()
-    rt = srv.run(arrivals, scans, realtime=True).summary()
+    gc.collect()
+    gc.disable()
+    try:
+        rt = srv.run(arrivals, scans, realtime=True).summary()
+    finally:
+        gc.enable()
     srv.close()
     srv = server()
-    sat = srv.run(arrivals, scans, realtime=False).summary()
+    gc.collect()
+    gc.disable()
+    try:
+        sat = srv.run(arrivals, scans, realtime=False).summary()
+    finally:
+        gc.enable()
     srv.close()
     # the plain path on the same requests: one update + extraction + readback per scan, in order
     maps = {i: gv.VoxelMap(nx=sp.nx, ny=sp.ny, nz=sp.nz, res=sp.res, neg_max_px=int(math.ceil(2.0 / sp.res)))
