@@ -42,6 +42,8 @@ def test_config_default(lib):
     ("nx", 0), ("nz", 5000), ("res", 0.0), ("res", -0.1), ("max_range", 0.0), ("hard_den", 0),
     ("hard_num", 3), ("slope_n", 4), ("slope_n", 17), ("slope_min_px", 2), ("neg_max_px", 0),
     ("scan_buffer", -1), ("scan_buffer", 65), ("obs_max_h", 0.1), ("hard_den", 70000),
+    ("neg_max_px", 65), ("slope_min_px", 26), ("res", float("inf")), ("neg_thresh", float("nan")),
+    ("obs_min_h", -0.1),
 ])
 def test_create_rejects_invalid_config_before_device_work(lib, field, value):
     c = gv.gvom_config_default()
