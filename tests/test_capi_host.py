@@ -92,3 +92,31 @@ def test_config_limit_on_range_over_resolution(lib):
     c.res, c.max_range = 0.01, 100.0  # 10,000 voxels of range: beyond the 8192 limit
     h = ctypes.c_void_p()
     assert lib.gvom_create(ctypes.byref(c), ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG
+
+
+def test_batch_and_noalloc_reject_invalid_arguments(lib):
+    h = ctypes.c_void_p(1234)
+    assert lib.gvom_batch_create(0, 10, 0, ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG and h.value is None
+    h = ctypes.c_void_p(1234)
+    assert lib.gvom_batch_create(4097, 10, 0, ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG and h.value is None
+    assert lib.gvom_batch_create(1, 0, 0, ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_batch_create(1, 10, 2, ctypes.byref(h)) == gv.GVOM_ERR_INVALID_ARG  # unknown flag
+    assert lib.gvom_batch_create(1, 10, 0, None) == gv.GVOM_ERR_INVALID_ARG
+    assert lib.gvom_batch_set_tuning(None, None) == gv.GVOM_ERR_INVALID_ARG
+    T = (ctypes.c_double * 12)()
+    v = (ctypes.c_double * 3)()
+    ns = (ctypes.c_int64 * 1)(0)
+    ptrs = (ctypes.c_void_p * 1)()
+    assert lib.gvom_batch_step(None, ptrs, 1, v, ptrs, ns, 3, T, None, None) == gv.GVOM_ERR_INVALID_ARG
+    lib.gvom_batch_destroy(None)  # no-op
+    # the no-alloc extraction validates the configuration and its map-size
+    # limit (512 x 512 pixels) before any launch
+    out = gv.gvom_maps_out()
+    fake = ctypes.c_void_p(256)
+    assert lib.gvom_extract_maps_noalloc(None, fake, fake, fake, ctypes.byref(out), None) == gv.GVOM_ERR_INVALID_ARG
+    c = gv.gvom_config_default()
+    assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), None, fake, fake, ctypes.byref(out), None) == \
+        gv.GVOM_ERR_INVALID_ARG
+    c.nx, c.ny = 1024, 512
+    assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), fake, fake, fake, ctypes.byref(out), None) == \
+        gv.GVOM_ERR_INVALID_ARG
