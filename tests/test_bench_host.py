@@ -1,0 +1,53 @@
+"""Host checks of the benchmark's reporting arithmetic (no GPU): the step
+roofline rule, the traffic record lookup keyed by the CUDA sources' digest,
+and the host description of the CPU baselines."""
+import os
+import types
+
+import pytest
+
+import bench
+
+
+def test_roofline_step_is_the_larger_of_atomics_and_bytes():
+    ms = types.SimpleNamespace(nx=256, ny=256, nz=64)
+    V = ms.nx * ms.ny * ms.nz
+    # 5.6 M atomics at 200 G/s = 28 us; bytes 12 * 131072 + 12 * V + 17 * 65536 at 6753 GB/s
+    r = bench.roofline_step(5.6e6, 200e9, V, ms, 131072, 6753.0, 80e-6)
+    hbm_bytes = 12 * 131072 + 12 * V + 17 * 65536
+    assert r["atomic_us"] == pytest.approx(28.0)
+    assert r["hbm_us"] == pytest.approx(1e6 * hbm_bytes / 6753e9)
+    assert r["roofline_us"] == pytest.approx(max(r["atomic_us"], r["hbm_us"]))
+    assert r["serial_roofline_us"] == pytest.approx(r["atomic_us"] + r["hbm_us"])
+    assert r["frac"] == pytest.approx(r["roofline_us"] / 80.0)
+    # an HBM-bound case: few atomics
+    r2 = bench.roofline_step(1e3, 200e9, V, ms, 131072, 6753.0, 80e-6)
+    assert r2["roofline_us"] == pytest.approx(r2["hbm_us"])
+
+
+def test_traffic_record_matches_the_current_sources():
+    # the committed record names the digest of the CUDA sources; a lookup
+    # for a workload it does not hold gives nothing
+    v = bench.profile_traffic("k_ingest", "plain_sequence")
+    assert v is None or v > 1e6
+    assert bench.profile_traffic("k_ingest", "no_such_workload") is None
+
+
+def test_traffic_record_ignores_a_stale_digest(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.txt").write_text("kernel=k_ingest workload=w src=0000000000000000 dram_bytes_per_launch=5\n")
+    csrc = tmp_path / "paper_2109_13176_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "a.cu").write_text("// kernel\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profile_traffic("k_ingest", "w") is None
+    import hashlib
+    digest = hashlib.sha256(b"// kernel\n").hexdigest()[:16]
+    (prof / "traffic.txt").write_text(f"kernel=k_ingest workload=w src={digest} dram_bytes_per_launch=5\n")
+    assert bench.profile_traffic("k_ingest", "w") == 5.0
+
+
+def test_host_cpu_description():
+    h = bench.host_cpu()
+    assert h["nproc"] == (os.cpu_count() or 0) and isinstance(h["model"], str) and h["model"]
