@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=10, help="timed steps of the batched leg")
     ap.add_argument("--retune", action="store_true", help="ignore cached tuning and search again")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
-    ap.add_argument("--served-seconds", type=float, default=20.0, help="length of the replayed arrival stream")
+    ap.add_argument("--served-seconds", type=float, default=60.0, help="length of the replayed arrival stream")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
     ap.add_argument("--no-high-speed", action="store_true", help="skip the 512x512x64 high-speed leg")
     ap.add_argument("--high-speed-scans", type=int, default=8, help="generated scans of the high-speed leg")
