@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--served-seconds", type=float, default=60.0, help="length of the replayed arrival stream")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
     ap.add_argument("--no-high-speed", action="store_true", help="skip the 512x512x64 high-speed leg")
-    ap.add_argument("--high-speed-scans", type=int, default=8, help="generated scans of the high-speed leg")
+    ap.add_argument("--high-speed-scans", type=int, default=40, help="generated scans of the high-speed leg")
     ap.add_argument("--workload", choices=["sequence", "high_speed"], default="sequence",
                     help="workload of the main leg (high_speed also drops the separate high-speed leg)")
     return ap.parse_args()
