@@ -120,3 +120,19 @@ def test_batch_and_noalloc_reject_invalid_arguments(lib):
     c.nx, c.ny = 1024, 512
     assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), fake, fake, fake, ctypes.byref(out), None) == \
         gv.GVOM_ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback_without_a_gpu(lib, monkeypatch):
+    # the product path fails loudly: no device, no map; no library, no calls
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    c = gv.gvom_config_default()
+    h = ctypes.c_void_p()
+    assert lib.gvom_create(ctypes.byref(c), ctypes.byref(h)) == gv.GVOM_ERR_CUDA and h.value is None
+    with pytest.raises(RuntimeError):
+        gv.VoxelMap(nx=16, ny=16, nz=8, res=0.2)
+    monkeypatch.setattr(gv, "_lib", None)
+    monkeypatch.setattr(gv, "LIB_PATH", "/nonexistent/libgvom.so")
+    with pytest.raises(RuntimeError):
+        gv.load_library()
