@@ -193,8 +193,12 @@ GVOM_API int gvom_reset(struct gvom_map* map, const int64_t origin[3], gvom_stre
 GVOM_API int gvom_shift(struct gvom_map* map, const int64_t new_origin[3], gvom_stream_t stream);
 
 /* Folds one scan into the map (Sec. III-C, Sec. III-D combination rule):
- * each point is transformed by T_ws (FP64, no fused multiply-add),
- * filtered, and quantised to 1/256 voxel; the endpoint voxel gains a hit
+ * each point is transformed by T_ws in FP64, each world coordinate
+ * w_i = fma(T[i][2], pz, fma(T[i][1], py, fma(T[i][0], px, T[i][3])))
+ * with every fused multiply-add rounded once, in this order; points are
+ * kept iff finite with 0 < fma(pz, pz, fma(py, py, px * px)) <=
+ * max_range^2 (FP64); each coordinate is quantised to 1/256 voxel as
+ * round-half-even(fma(w, 256 / res, -256 origin)); the endpoint voxel gains a hit
  * and its lowest-return height is lowered to the point's z (float32);
  * every other window voxel the sensor-to-point segment meets (half-open
  * voxels, exact integer traversal) gains a pass. pts_dev: n points,
@@ -227,9 +231,15 @@ GVOM_API int gvom_extract_maps(struct gvom_map* map, const gvom_maps_out* out, g
  * device array inside the library, 512 x 512 pixels (1 MiB) at most, which
  * every GPU that loads the library holds until the process exits.
  * Limits and errors: cfg must be valid and nx * ny <= 262144, else
- * GVOM_ERR_INVALID_ARG with nothing enqueued.
+ * GVOM_ERR_INVALID_ARG with nothing enqueued. Alignment: when nz is a
+ * multiple of 4 the three grids must start on 16-byte boundaries (they are
+ * read with 16-byte loads), else on 4-byte ones; the float outputs on
+ * 4-byte ones; a misaligned pointer is GVOM_ERR_INVALID_ARG.
  * Set-up: the first call on each device looks the array up (with that
- * device current); make that first call before any stream capture.
+ * device current); make that first call before any stream capture. A first
+ * call made while `stream` is capturing returns GVOM_ERR_INVALID_ARG and
+ * enqueues nothing. The looked-up address lives until the process exits:
+ * do not use the library across a cudaDeviceReset.
  * Sharing: all calls on a device share the array and it keeps the last
  * call's contents (every pixel is rewritten before it is read, so nothing
  * needs clearing); calls that may overlap on the GPU (different streams

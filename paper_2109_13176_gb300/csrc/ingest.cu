@@ -5,8 +5,9 @@
 // of traversal work (a ray crosses anywhere from one to several hundred
 // voxels, and one thread per ray leaves the GPU idle behind the longest):
 //
-//  k_rays   one thread per lidar point: FP64 transform without fused
-//           operations, filter, quantisation to 1/256 voxel, the hit and
+//  k_rays   one thread per lidar point: FP64 transform as a fixed chain
+//           of fused multiply-adds per row (see xform_row), filter,
+//           quantisation to 1/256 voxel, the hit and
 //           lowest-return update of the endpoint voxel, and the split of
 //           the ray's in-window traversal into segments of at most
 //           seg_len voxel slabs along its major axis, appended to a work

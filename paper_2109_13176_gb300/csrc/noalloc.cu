@@ -29,22 +29,32 @@ float* g_height_ptr[kMaxDevices] = {};
 // Device address of g_noalloc_height on the current device. Host code may
 // not pass the symbol itself to a kernel (on the host it names a host-side
 // shadow, not device memory), so the address is looked up once per device
-// with that device current, and cached.
-cudaError_t noalloc_height_scratch(float** out) {
+// with that device current, and cached. The first look-up may load the
+// library's device code, which must not happen while `stream` is being
+// captured into a graph: that first call is refused then (GVOM_ERR_INVALID_ARG,
+// nothing enqueued). A device reset (cudaDeviceReset) invalidates the cached
+// address, as it invalidates every map; the library must not be used across one.
+int noalloc_height_scratch(cudaStream_t stream, float** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (e != cudaSuccess) return GVOM_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return GVOM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mu);
     if (g_height_ptr[dev] == nullptr) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        e = cudaStreamIsCapturing(stream, &cs);
+        if (e != cudaSuccess) return GVOM_ERR_CUDA;
+        if (cs != cudaStreamCaptureStatusNone) return GVOM_ERR_INVALID_ARG;
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_height);
-        if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return GVOM_ERR_CUDA;
         g_height_ptr[dev] = static_cast<float*>(p);
     }
     *out = g_height_ptr[dev];
-    return cudaSuccess;
+    return GVOM_OK;
 }
+
+bool aligned(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 0; }
 
 }  // namespace
 
@@ -52,12 +62,20 @@ extern "C" int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t*
                                          const float* minz_dev, const gvom_maps_out* out, gvom_stream_t stream) {
     if (!gvom::valid_config(cfg) || !hits_dev || !passes_dev || !minz_dev || !out) return GVOM_ERR_INVALID_ARG;
     if ((long long)cfg->nx * cfg->ny > kNoallocMaxPixels) return GVOM_ERR_INVALID_ARG;
+    // The column pass reads a grid whose nz is a multiple of 4 with 16-byte
+    // loads; other grids and the float outputs need their element alignment.
+    const uintptr_t grid_align = (cfg->nz & 3) == 0 ? 16 : 4;
+    if (!aligned(hits_dev, grid_align) || !aligned(passes_dev, grid_align) || !aligned(minz_dev, grid_align))
+        return GVOM_ERR_INVALID_ARG;
+    if (!aligned(out->height_dev, 4) || !aligned(out->density_dev, 4) || !aligned(out->slope_dev, 4) ||
+        !aligned(out->roughness_dev, 4))
+        return GVOM_ERR_INVALID_ARG;
     float* height = out->height_dev;
     if (height == nullptr) {
-        const cudaError_t e = noalloc_height_scratch(&height);
-        if (e != cudaSuccess) {
+        const int rc = noalloc_height_scratch((cudaStream_t)stream, &height);
+        if (rc != GVOM_OK) {
             cudaGetLastError();
-            return GVOM_ERR_CUDA;
+            return rc;
         }
     }
     gvom::ExtractParams p;

@@ -122,6 +122,31 @@ def test_batch_and_noalloc_reject_invalid_arguments(lib):
         gv.GVOM_ERR_INVALID_ARG
 
 
+def test_noalloc_rejects_misaligned_grids_before_any_launch(lib):
+    # nz % 4 == 0: the grids are read with 16-byte loads, so a grid that
+    # starts 4 bytes into an allocation (a torch slice, say) is refused with
+    # an error instead of faulting on the device; other nz need 4 bytes.
+    # These fake device addresses are never dereferenced: the checks come
+    # before any CUDA call (this test runs without a GPU).
+    c = gv.gvom_config_default()      # nz = 32
+    out = gv.gvom_maps_out()
+    ok, off4, off2 = ctypes.c_void_p(4096), ctypes.c_void_p(4096 + 4), ctypes.c_void_p(4096 + 2)
+    for grids in ((off4, ok, ok), (ok, off4, ok), (ok, ok, off4)):
+        assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), *grids, ctypes.byref(out), None) == \
+            gv.GVOM_ERR_INVALID_ARG
+    c.nz = 30
+    for grids in ((off2, ok, ok), (ok, off2, ok), (ok, ok, off2)):
+        assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), *grids, ctypes.byref(out), None) == \
+            gv.GVOM_ERR_INVALID_ARG
+    # misaligned float outputs
+    c.nz = 32
+    for k in ("height_dev", "density_dev", "slope_dev", "roughness_dev"):
+        o = gv.gvom_maps_out()
+        setattr(o, k, 4096 + 2)
+        assert lib.gvom_extract_maps_noalloc(ctypes.byref(c), ok, ok, ok, ctypes.byref(o), None) == \
+            gv.GVOM_ERR_INVALID_ARG
+
+
 def test_no_cpu_fallback_without_a_gpu(lib, monkeypatch):
     # the product path fails loudly: no device, no map; no library, no calls
     torch = pytest.importorskip("torch")

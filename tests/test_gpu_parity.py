@@ -300,3 +300,61 @@ def test_pixel_tiles_for_large_search_distances(gv, nx, ny, halo):
     compare_voxels(gm, om)
     out, ref = compare_products(gm, om)
     assert (ref["flags"] & 8).any() and np.isfinite(ref["slope"]).sum() > nx * ny // 5
+
+
+# Hand-built height grids for the value of one cone (Sec. III-D, Fig. 4
+# caption): a ring with several defined heights (the cone's value is the
+# ring's lowest), a cone that stops at its first ring with ground, a corner
+# cell shared by two cones, and a ring reaching past the grid edge. The
+# expected Delta H at the test pixel is worked out by hand (the same grids
+# pin the oracle on CPU in test_oracle_products.py); here the device flags
+# must equal the oracle's on every pixel and show that Delta H.
+def _pins(dh):
+    """Delta H is exactly dh: flagged just below it, not at it (strict)."""
+    return [(float(np.nextafter(np.float32(dh), np.float32(-np.inf))), True), (float(dh), False)]
+
+
+CONE_CASES = [
+    # (cells (x, y, height), test pixel, [(threshold, negative expected)])
+    ([(9, 4, 0.5), (9, 5, 0.125), (9, 6, 0.375), (9, 7, 0.75), (9, 8, 0.625), (4, 6, 2.0)], (6, 6), _pins(1.875)),
+    ([(9, 8, 0.5), (9, 7, 0.125), (9, 6, 0.375), (9, 5, 0.75), (9, 4, 0.625), (4, 6, 2.0)], (6, 6), _pins(1.875)),
+    ([(9, 4, 0.5), (9, 5, 0.125), (9, 6, 0.375), (9, 7, 0.75), (9, 8, 0.625), (4, 6, -1.0)], (6, 6), _pins(1.125)),
+    ([(7, 6, 1.0), (8, 6, 0.0), (5, 6, 0.75)], (6, 6), _pins(0.25)),
+    # corner (8, 8) in both the +x and the +y cone: two values of 0.0
+    ([(8, 8, 0.0), (9, 6, 1.0), (6, 9, 0.5)], (6, 6), [(-0.125, True), (0.0, False), (0.3, False)]),
+    ([(9, 0, 0.75), (4, 1, 0.0)], (6, 1), _pins(0.75)),
+    # (12, 1) lies beyond the search distance: one value only
+    ([(12, 1, 0.75), (4, 1, 0.0)], (6, 1), [(-0.125, False), (0.3, False)]),
+]
+
+
+def _voxels_for_heights(cells, nx, ny, nz):
+    """One occupied voxel (iz = 0) per defined pixel, its lowest return the
+    pixel's height; every other voxel empty."""
+    hits = np.zeros((nx, ny, nz), np.uint32)
+    passes = np.zeros((nx, ny, nz), np.uint32)
+    minz = np.full((nx, ny, nz), np.inf, np.float32)
+    for x, y, h in cells:
+        hits[x, y, 0] = 1
+        minz[x, y, 0] = h
+    return hits, passes, minz
+
+
+@pytest.mark.parametrize("case", range(len(CONE_CASES)))
+def test_cone_values_on_hand_built_grids(gv, case):
+    cells, px, checks = CONE_CASES[case]
+    nx = ny = 13
+    nz = 4
+    hits, passes, minz = _voxels_for_heights(cells, nx, ny, nz)
+    dev = [torch.from_numpy(a.reshape(-1).view(np.int32) if a.dtype == np.uint32 else a.reshape(-1)).cuda()
+           for a in (hits, passes, minz)]
+    for th, expect in checks:
+        p = oracle.OracleParams(nx=nx, ny=ny, nz=nz, res=0.2, neg_max_px=5, neg_thresh=th)
+        ref = oracle.extract(p, hits, passes, minz)
+        assert bool(ref["flags"][px] & 8) == expect, (case, th)
+        h = torch.empty((nx, ny), device="cuda")
+        flags = torch.full((nx, ny), 255, dtype=torch.uint8, device="cuda")
+        gv.gvom_extract_maps_noalloc(gpu_config(gv, p), dev[0], dev[1], dev[2], height=h, flags=flags)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(h.cpu().numpy(), ref["height"])
+        np.testing.assert_array_equal(flags.cpu().numpy(), ref["flags"])

@@ -223,6 +223,96 @@ def test_negative_threshold_is_strict_and_distance_bounded():
     assert not np.any(f2 & 8)
 
 
+# --- the value of one cone (Sec. III-D, Fig. 4 caption) --------------------
+# Reading: a cone's assumed height is the lowest height on the first ring
+# (Chebyshev distance d) where it holds a defined in-grid pixel; corner cells
+# (|j| = d) belong to both cones that meet there; in-grid cells of a ring that
+# also reaches past the grid edge still count. The grids below are built by
+# hand so that each alternative reading flags the test pixel differently;
+# every expected value is worked out in the comments. Heights are multiples
+# of 1/8, so every Delta H is exact in float32 and float64.
+
+def _thresh_pins(params, grid, px, dh):
+    """Delta H at pixel px is exactly dh: flagged just below, not at dh
+    (strict threshold)."""
+    params.neg_thresh = float(np.nextafter(np.float32(dh), np.float32(-np.inf)))
+    assert oracle.negative(params, grid)[px] & 8, "flag expected just below Delta H"
+    params.neg_thresh = float(dh)
+    assert not oracle.negative(params, grid)[px] & 8, "no flag expected at Delta H"
+
+
+def test_cone_value_is_ring_minimum_not_first_last_axis_max_or_mean():
+    # P = (6, 6) undefined in a 13 x 13 grid, search distance 5.
+    # +x cone, ring 3 = cells (9, 3..9); five non-corner cells defined:
+    #   (9,4) 0.5  (9,5) 0.125  (9,6) 0.375 (on the axis)  (9,7) 0.75  (9,8) 0.625
+    # -x cone, ring 2: the single cell (4, 6) = 2.0 (its value under any reading).
+    # No other cone reaches a defined cell. Delta H = 2.0 - v(+x):
+    #   ring minimum 0.125 -> 1.875 (the reading)
+    #   first cell in ring order 0.5 -> 1.5, last 0.625 -> 1.375,
+    #   axis cell 0.375 -> 1.625, ring maximum 0.75 -> 1.25, mean 0.475 -> 1.525.
+    params = oracle.OracleParams(nx=13, ny=13, nz=4, res=0.2, neg_max_px=5)
+    g = _grid_from([(9, 4, 0.5), (9, 5, 0.125), (9, 6, 0.375), (9, 7, 0.75), (9, 8, 0.625), (4, 6, 2.0)], 13, 13)
+    _thresh_pins(params, g, (6, 6), 1.875)
+    # the same ring in reverse order: first and last swap, the minimum stays
+    g2 = _grid_from([(9, 8, 0.5), (9, 7, 0.125), (9, 6, 0.375), (9, 5, 0.75), (9, 4, 0.625), (4, 6, 2.0)], 13, 13)
+    _thresh_pins(params, g2, (6, 6), 1.875)
+    # an upper reference: Delta H = v(+x) - (-1.0) = 1.125 with the ring
+    # minimum (the ring maximum would give 1.75)
+    g3 = _grid_from([(9, 4, 0.5), (9, 5, 0.125), (9, 6, 0.375), (9, 7, 0.75), (9, 8, 0.625), (4, 6, -1.0)], 13, 13)
+    _thresh_pins(params, g3, (6, 6), 1.125)
+
+
+def test_cone_stops_at_first_ring_with_ground_not_at_a_nearer_cell_further_out():
+    # P = (6, 6); +x ring 1 holds (7, 6) = 1.0 only; ring 2 holds a lower cell
+    # (8, 6) = 0.0 that the cone never reaches. -x ring 1: (5, 6) = 0.75.
+    # Values {1.0, 0.75}: Delta H = 0.25. A cone that took the lowest height
+    # within the search distance would give {0.0, 0.75}: Delta H = 0.75.
+    params = oracle.OracleParams(nx=13, ny=13, nz=4, res=0.2, neg_max_px=5)
+    g = _grid_from([(7, 6, 1.0), (8, 6, 0.0), (5, 6, 0.75)], 13, 13)
+    _thresh_pins(params, g, (6, 6), 0.25)
+
+
+def test_corner_cell_belongs_to_both_cones():
+    # P = (6, 6). The corner (8, 8) = 0.0 lies on ring 2 of both the +x cone
+    # (cells (8, 4..8)) and the +y cone (cells (4..8, 8)). Further out:
+    # (9, 6) = 1.0 on +x ring 3 and (6, 9) = 0.5 on +y ring 3. -x and -y
+    # find nothing. Threshold 0.3:
+    #   corner in both cones: +x = 0.0, +y = 0.0 -> Delta H 0 -> not negative
+    #   corner only in +x:    +x = 0.0, +y = 0.5 -> 0.5 -> negative
+    #   corner only in +y:    +y = 0.0, +x = 1.0 -> 1.0 -> negative
+    #   corner in neither:    +x = 1.0, +y = 0.5 -> 0.5 -> negative
+    params = oracle.OracleParams(nx=13, ny=13, nz=4, res=0.2, neg_max_px=5, neg_thresh=0.3)
+    g = _grid_from([(8, 8, 0.0), (9, 6, 1.0), (6, 9, 0.5)], 13, 13)
+    assert not oracle.negative(params, g)[6, 6] & 8
+    # two values are there (0.0 twice): any threshold below 0 flags the pixel,
+    # which one value alone never does
+    params.neg_thresh = -0.125
+    assert oracle.negative(params, g)[6, 6] & 8
+    assert not oracle.negative(params, _grid_from([(9, 6, 1.0)], 13, 13))[6, 6] & 8
+    # the other three corners of ring 2, each with the +x/-x/+y/-y cones they join
+    for (cx, cy) in ((4, 8), (4, 4), (8, 4)):
+        params.neg_thresh = -0.125
+        assert oracle.negative(params, _grid_from([(cx, cy, 0.0)], 13, 13))[6, 6] & 8
+
+
+def test_cone_ring_partly_outside_the_grid_keeps_searching():
+    # P = (6, 1) near the y = 0 edge of a 13 x 13 grid.
+    # +x cone: ring 2 = (8, -1..3) reaches past the edge at (8, -1) and has no
+    # defined in-grid cell; ring 3 = (9, -2..4) holds (9, 0) = 0.75.
+    # -x cone, ring 2: (4, 1) = 0.0. -y cone: ring 1 = (5..7, 0) empty, ring 2
+    # would be y = -1, off the grid: the cone stops without a value. +y finds
+    # nothing. Values {0.75, 0.0}: Delta H = 0.75. A cone that gave up at
+    # the first ring reaching past the edge would leave one value: no flag.
+    params = oracle.OracleParams(nx=13, ny=13, nz=4, res=0.2, neg_max_px=5)
+    g = _grid_from([(9, 0, 0.75), (4, 1, 0.0)], 13, 13)
+    _thresh_pins(params, g, (6, 1), 0.75)
+    # a defined cell beyond the search distance does not count: (12, 1) is
+    # on +x ring 6 > 5
+    g2 = _grid_from([(12, 1, 0.75), (4, 1, 0.0)], 13, 13)
+    params.neg_thresh = -0.125
+    assert not oracle.negative(params, g2)[6, 1] & 8
+
+
 # --- qualitative scene outcomes (the single-scan test scene) ---------------
 @pytest.fixture(scope="module")
 def single_scan_maps():
