@@ -1,18 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 voxel map update (G-VOM per-scan update).
 
-Workload (default): the plain sequence -- a 64-beam lidar (131,072 points
-per scan), 20 scans at 10 Hz along a 4.5 m/s sinusoidal path over seeded
-procedural terrain, into a 256 x 256 x 64 map at 0.2 m with a window shift
-every scan. One step = one scan through the whole path: shift the window,
-ingest the scan (transform, hits, exact traversal passes), and extract every
-2D product (height, obstacles, density, slope, roughness, negative
-obstacles). Steps cycle through the 20 scans.
+Workload (default, the headline): the plain high-speed workload -- a
+128-beam lidar (262,144 points per scan) at 12 m/s over seeded procedural
+terrain with vegetation clusters, 40 scans at 10 Hz into a 512 x 512 x 64
+map at 0.1 m (201 MB of counts, more than the 129 MB L2) with a window
+shift every scan. One step = one scan through the whole path: shift the
+window, ingest the scan (transform, hits, exact traversal passes), and
+extract every 2D product (height, obstacles, density, slope, roughness,
+negative obstacles). Steps cycle through the 40 scans.
 
-Also measured (key "high_speed"): the high-speed workload -- a 128-beam
-lidar (262,144 points per scan) at 12 m/s into a 512 x 512 x 64 map at
-0.1 m, whose 201 MB of counts exceed L2. --workload high_speed makes it the
-main leg instead (both arms).
+Also measured (key "sequence"): the plain sequence workload -- a 64-beam
+lidar (131,072 points per scan), 20 scans along a 4.5 m/s sinusoidal path,
+into a 256 x 256 x 64 map at 0.2 m. --workload sequence swaps the two
+(both arms). The batched (64 maps), served (32 robots) and next-row legs
+(pipeline, lookup-table export, scan buffer, several sensors) follow.
 
 Metric: rays integrated per second (valid rays / GPU time), with map updates
 per second beside it. The L2 is flushed (a 256 MiB write) between timed
@@ -40,10 +42,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "rays integrated/s (plain sequence map update: shift + ingest + extract)"
+METRIC = "rays integrated/s (plain high-speed map update: shift + ingest + extract)"
 UNIT = "rays/s"
-WORKLOAD = "plain sequence: 64-beam 64x2048 = 131,072 pts/scan, 20 scans at 10 Hz, 4.5 m/s, map 256x256x64 @ 0.2 m, shift every scan"
-METRIC_HIGH_SPEED = "rays integrated/s (plain high-speed map update: shift + ingest + extract)"
+METRIC_SEQUENCE = "rays integrated/s (plain sequence map update: shift + ingest + extract)"
+SEQUENCE_WORKLOAD = ("plain sequence: 64-beam 64x2048 = 131,072 pts/scan, 20 scans at 10 Hz, 4.5 m/s, "
+                     "map 256x256x64 @ 0.2 m, shift every scan")
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -62,10 +65,11 @@ def parse():
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--served-seconds", type=float, default=60.0, help="length of the replayed arrival stream")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
-    ap.add_argument("--no-high-speed", action="store_true", help="skip the 512x512x64 high-speed leg")
-    ap.add_argument("--high-speed-scans", type=int, default=40, help="generated scans of the high-speed leg")
-    ap.add_argument("--workload", choices=["sequence", "high_speed"], default="sequence",
-                    help="workload of the main leg (high_speed also drops the separate high-speed leg)")
+    ap.add_argument("--no-other", action="store_true",
+                    help="skip the other plain workload's leg (sequence when the main leg is high_speed)")
+    ap.add_argument("--high-speed-scans", type=int, default=40, help="generated scans of the high-speed workload")
+    ap.add_argument("--workload", choices=["sequence", "high_speed"], default="high_speed",
+                    help="workload of the main leg; the other one is measured as a sub-object")
     return ap.parse_args()
 
 
@@ -109,7 +113,8 @@ def host_cpu() -> dict:
     return {"nproc": os.cpu_count() or 0, "model": model or platform.machine()}
 
 
-def make_inputs(rank: int, workload: str = "sequence", n_scans: int = 8):
+def make_inputs(rank: int, workload: str = "high_speed", n_scans: int = 40):
+    """The plain workload's scans (high_speed: the first n_scans of 40)."""
     if workload == "high_speed":
         return make_high_speed_inputs(rank, n_scans)
     import synth
@@ -118,19 +123,30 @@ def make_inputs(rank: int, workload: str = "sequence", n_scans: int = 8):
     return cfg, scans
 
 
+def workload_text(workload: str, n_scans: int) -> str:
+    return HIGH_SPEED_WORKLOAD.format(n=n_scans) if workload == "high_speed" else SEQUENCE_WORKLOAD
+
+
+def metric_of(workload: str) -> str:
+    return METRIC if workload == "high_speed" else METRIC_SEQUENCE
+
+
 BATCHED_WORKLOAD = ("batched: {m} independent maps 256x256x64 @ 0.2 m, each its own terrain and trajectory, "
                     "scan sizes log-uniform in [8,192, 262,144] (subsets of a 128x2048 scan), 2 generated steps cycled")
 
 
 SERVED_WORKLOAD = ("served: 32 robots, mixed sensors (16/64/128 beams) and maps (128x128x32 @ 0.2 m, "
                    "256x256x64 @ 0.2 m, 512x512x64 @ 0.1 m), exponential inter-arrival times (mean 100 ms), "
-                   "{s:g} s stream replayed in real time, each robot cycling a pool of 4 consecutive scans")
+                   "{s:g} s stream replayed in real time; each arrival posed on its robot's own trajectory "
+                   "(2-12 m/s), its points one of 8 casts per robot spread over the stream")
+SERVED_LOADS = (2.0, 4.0, 8.0, 16.0)   # offered-load factors of the sweep
+SERVED_SWEEP_WINDOW_S = 10.0           # replay window per sweep point
 
 
 def make_served_inputs(rank: int, seconds: float):
     import synth
-    return synth.served_requests(n_robots=32, duration_s=seconds, pool=4, seed=synth.SEEDS["served"] + 1000 * rank,
-                                 workers=gen_workers())
+    return synth.served_stream(n_robots=32, duration_s=seconds, seed=synth.SEEDS["served"] + 1000 * rank,
+                               workers=gen_workers())
 
 
 HIGH_SPEED_WORKLOAD = ("plain high-speed: 128-beam 128x2048 = 262,144 pts/scan at 10 Hz, 12 m/s, map 512x512x64 @ 0.1 m "
@@ -230,15 +246,14 @@ def oracle_served_baseline(inputs, time_budget_s: float):
     maps = {}
     rays, n, t_all = 0, 0, time.perf_counter()
     per = []
-    for _, rid, k in arrivals:
+    for _, rid, k, c, T, veh in arrivals:
         r = robots[rid]
         om = maps.get(rid)
         if om is None:
             om = maps[rid] = oracle.OracleMap(oracle_params(r["map"]))
-        s = r["scans"][k]
         t0 = time.perf_counter()
-        om.shift_for_pose(s.vehicle_xyz)
-        rays += om.ingest(s.points, s.T_ws).rays_valid
+        om.shift_for_pose(veh)
+        rays += om.ingest(r["casts"][c].points, T).rays_valid
         om.extract()
         per.append(time.perf_counter() - t0)
         n += 1
@@ -366,18 +381,19 @@ def profile_traffic(kernel: str, workload: str):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    hs = args.workload == "high_speed"
-    cfg, scans = make_inputs(0, args.workload, args.high_speed_scans)
-    res = run_oracle_steps(cfg, scans, args.warmup + args.steps)
+    # the steps cycle the workload's scans; only the ones they reach are cast
+    n = args.warmup + args.steps
+    cfg, scans = make_inputs(0, args.workload, max(1, min(args.high_speed_scans, n)))
+    res = run_oracle_steps(cfg, scans, n)
     timed = res[args.warmup:]
     rays = sum(r for r, _ in timed)
     secs = sum(t for _, t in timed)
     v = rays / secs
-    line = {"impl": "reference", "metric": METRIC_HIGH_SPEED if hs else METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric_of(args.workload), "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded procedural terrain and lidar model)",
-            "config": {"workload": HIGH_SPEED_WORKLOAD.format(n=len(scans)) if hs else WORKLOAD,
+            "config": {"workload": workload_text(args.workload, args.high_speed_scans),
                        "map": [cfg.map.nx, cfg.map.ny, cfg.map.nz], "res_m": cfg.map.res,
                        "points_per_scan": cfg.lidar.n, "scans": len(scans)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
@@ -461,11 +477,13 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
-def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush, stream, serial_e2e, hbm_peak):
+def run_next_rows(args, gv, torch, cfg, scans, tuning, flush, stream, serial_e2e, hbm_peak):
     """The widened rows on the plain-sequence workload: the asynchronous
     pipeline end to end, the lookup-table export, a 10-scan buffer, and four
     sensors per scan folded in one launch."""
     ms = cfg.map
+    dev_pts = [torch.from_numpy(s.points).cuda() for s in scans]
+    host_pts = [torch.from_numpy(s.points).pin_memory() for s in scans]
     kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
     n_steps = args.steps
     ns = len(scans)
@@ -501,7 +519,8 @@ def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush,
         rays = m.stats()["rays_valid"] - r0
     wall = statistics.median(walls)
     out["pipeline_e2e"] = {"value": rays / wall, "unit": UNIT, "ms_per_scan": 1e3 * wall / n_pipe,
-                           "vs_serial_e2e": rays / wall / serial_e2e, "depth": 3, "scans_per_window": n_pipe,
+                           "vs_serial_e2e": rays / wall / serial_e2e if serial_e2e else None, "depth": 3,
+                           "scans_per_window": n_pipe,
                            "timing": "host wall clock from submit of the first scan to the last scan's products "
                                      "in pinned host memory, median of three windows; steps overlap, so L2 is "
                                      "not flushed between them"}
@@ -600,124 +619,216 @@ def run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush,
     return out
 
 
-def run_high_speed(args, gv, tune, torch, inputs, flush, stream, hbm_peak):
-    """The high-speed workload on one map of 512 x 512 x 64 at 0.1 m: the
-    same timed step as the main leg (shift + ingest + extract, events per
-    step, L2 flushed between steps). Its state (201 MB of counts) does not
-    fit in L2, so the walk's atomics and the column pass meet HBM."""
+def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=None, e2e_steps=200):
+    """One plain workload through the public API: the timed steps (shift +
+    ingest + extract, CUDA events per step on the launching stream, L2
+    flushed between steps, one synchronisation at the end), then the same
+    update end to end with host buffers (pinned H2D copy of the scan,
+    gvom_update_extract, one D2H copy of the packed products, per step).
+    Returns the raw figures; the map is closed."""
+    import contextlib
     cfg, scans = inputs
     ms = cfg.map
-    dev = [torch.from_numpy(s.points).cuda() for s in scans]
-    m = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
-    o = m.alloc_maps()
-    nt = min(4, len(scans))
-    tuning, _ = tune.tune_map(m, dev[:nt], [s.T_ws for s in scans[:nt]], [s.vehicle_xyz for s in scans[:nt]],
-                              flush=flush, refresh=args.retune)
-    m.reset((0, 0, 0))
-    m.reset_stats()
     ns = len(scans)
+    dev_pts = [torch.from_numpy(s.points).cuda() for s in scans]
+    host_pts = [torch.from_numpy(s.points).pin_memory() for s in scans]
+    gmap = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
+    out = gmap.alloc_maps()
+    # launch shape for this workload: cached, or searched on its first scans
+    nt = min(4, ns)
+    tuning, tune_entry = tune.tune_map(gmap, dev_pts[:nt], [s.T_ws for s in scans[:nt]],
+                                       [s.vehicle_xyz for s in scans[:nt]], flush=flush, refresh=args.retune)
+    gmap.reset((0, 0, 0))
+    gmap.reset_stats()
 
-    def step(k, e_ing=None):
+    def step(k, ev_ingest0=None, ev_ingest1=None):
         s = scans[k % ns]
-        m.shift(m.origin_for_pose(s.vehicle_xyz))
-        m.ingest(dev[k % ns], s.T_ws)
-        if e_ing is not None:
-            e_ing.record(stream)
-        m.extract_maps(o)
+        gmap.shift(gmap.origin_for_pose(s.vehicle_xyz))
+        if ev_ingest0 is not None:
+            ev_ingest0.record(stream)
+        gmap.ingest(dev_pts[k % ns], s.T_ws)
+        if ev_ingest1 is not None:
+            ev_ingest1.record(stream)
+        gmap.extract_maps(out)
 
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
-    st0 = m.stats()
-    l0 = gv.gvom_kernel_launches()
-    evs = []
-    for i in range(args.steps):
-        flush()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record(stream)
-        step(args.warmup + i, e[1])
-        e[2].record(stream)
-        evs.append(e)
+    st0 = gmap.stats()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = gv.gvom_kernel_launches()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     torch.cuda.synchronize()
-    st1 = m.stats()
-    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
-    upd_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    ext_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    tot = sum(step_ms) * 1e-3
-    rays = st1["rays_valid"] - st0["rays_valid"]
-    visits = st1["pass_visits"] - st0["pass_visits"]
-    hits = st1["hits_in_window"] - st0["hits_in_window"]
+    gc.collect()
+    gc.disable()
+    with (clocks if clocks is not None else contextlib.nullcontext()):
+        for i in range(args.steps):
+            flush()
+            e = ev[i]
+            e[0].record(stream)
+            step(args.warmup + i, e[1], e[2])
+            e[3].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = gv.gvom_kernel_launches() - launches0  # this library's kernels only
+    st1 = gmap.stats()
+    r = {"step_ms": [e[0].elapsed_time(e[3]) for e in ev], "ingest_ms": [e[1].elapsed_time(e[2]) for e in ev],
+         "extract_ms": [e[2].elapsed_time(e[3]) for e in ev],
+         "shift_ms": [e[0].elapsed_time(e[1]) for e in ev],
+         "rays": st1["rays_valid"] - st0["rays_valid"], "visits": st1["pass_visits"] - st0["pass_visits"],
+         "hits": st1["hits_in_window"] - st0["hits_in_window"], "launches": launches,
+         "tuning": tuning, "tune_entry": tune_entry, "cfg": cfg, "n_scans": ns}
+    r["total_s"] = sum(r["step_ms"]) * 1e-3
+
+    # end to end through the public API with host buffers
+    h2d = sum(p.numel() * 4 for p in host_pts) / ns
+    packed_dev, packed_out = gmap.alloc_maps_packed()
+    packed_host = torch.empty(packed_dev.numel(), dtype=torch.uint8, pin_memory=True)
+    staging = torch.empty((max(int(p.shape[0]) for p in dev_pts), 3), dtype=torch.float32, device="cuda")
+    e2e_ms = []
+    for i in range(e2e_steps):
+        flush()
+        k = args.warmup + args.steps + i
+        s = scans[k % ns]
+        hp = host_pts[k % ns]
+        view = staging[:hp.shape[0]]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        view.copy_(hp, non_blocking=True)
+        gmap.update_extract(s.vehicle_xyz, view, s.T_ws, packed_out)
+        packed_host.copy_(packed_dev, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    gc.enable()
+    st2 = gmap.stats()
+    r.update({"e2e_ms": e2e_ms, "e2e_s": sum(e2e_ms) * 1e-3, "rays_e2e": st2["rays_valid"] - st1["rays_valid"],
+              "h2d": int(h2d), "d2h": int(packed_dev.numel())})
+    gmap.close()
+    return r
+
+
+def ingest_roofline(r, steps, red_peak, workload):
+    """The ingest (per-point pass + segment walk, one timed region) against
+    the measured L2 reduction-atomic rate."""
+    atom = (r["visits"] + 2 * r["hits"]) / steps
+    achieved = atom / (statistics.mean(r["ingest_ms"]) * 1e-3)
+    return {"kernel": "k_ingest", "bound": "l2_atomic", "achieved": achieved / 1e9, "peak": red_peak / 1e9,
+            "unit": "Gatomic/s", "frac": achieved / red_peak,
+            "traffic": profile_traffic("k_ingest", "plain_" + workload),
+            "peak_source": "measured in this run: scattered 32-bit reduction atomics over 64 MiB (gvom_microbench_red)",
+            "algorithmic": "pass visits + 2 atomics per in-window hit, per launch"}
+
+
+def extract_roofline(r, ms, hbm_peak, peak_kind):
     V = ms.nx * ms.ny * ms.nz
-    ext_bytes = 12 * V + 17 * ms.nx * ms.ny
-    ext_s = statistics.mean(ext_ms) * 1e-3
-    out = {"workload": HIGH_SPEED_WORKLOAD.format(n=ns), "value": rays / tot, "unit": UNIT,
-           "map_updates_per_s": args.steps / tot, "ms_per_step_mean": 1e3 * tot / args.steps,
-           "ms_per_step_median": statistics.median(step_ms), "rays_per_step": rays / args.steps,
-           "pass_visits_per_step": visits / args.steps, "hits_per_step": hits / args.steps,
-           "shift_ingest_ms_mean": statistics.mean(upd_ms), "extract_ms_mean": 1e3 * ext_s,
-           "ingest_atomics": {"per_step": (visits + 2 * hits) / args.steps,
-                              "achieved_g_per_s": (visits + 2 * hits) / (sum(upd_ms) * 1e-3) / 1e9,
-                              "note": "pass visits + 2 per in-window hit over shift + ingest time"},
-           "extract_hbm": {"algorithmic_bytes": ext_bytes, "achieved_gbs": ext_bytes / ext_s / 1e9,
-                           "frac": ext_bytes / ext_s / 1e9 / hbm_peak if hbm_peak else None,
-                           "bytes_rule": "12 B/voxel read + 17 B/px written"},
-           "gpu_launches_per_step": (gv.gvom_kernel_launches() - l0) / args.steps,
-           "tuning": {"seg_len": tuning[0], "march_block": tuning[1], "march_blocks_per_sm": tuning[2]},
-           "l2": "flushed between timed steps (256 MiB write)"}
-    m.close()
-    return out
+    b = 12 * V + (4 + 4 + 1 + 4 + 4) * ms.nx * ms.ny
+    t = statistics.mean(r["extract_ms"]) * 1e-3
+    return {"kernels": "k_columns + k_slope_negative", "bound": "hbm", "achieved": b / t / 1e9, "peak": hbm_peak,
+            "unit": "GB/s", "frac": b / t / 1e9 / hbm_peak if hbm_peak else None, "algorithmic_bytes": b,
+            "bytes_rule": "12 B/voxel read + 17 B/px written", "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
 
 
-def oracle_high_speed_baseline(inputs, time_budget_s: float):
-    """The oracle on the first scans of the high-speed workload (one thread)."""
+def e2e_object(r):
+    return {"value": r["rays_e2e"] / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+            "d2h_bytes_per_step": r["d2h"], "ms_per_step_p50": statistics.median(r["e2e_ms"]),
+            "ms_per_step_p99": sorted(r["e2e_ms"])[int(0.99 * (len(r["e2e_ms"]) - 1))], "steps": len(r["e2e_ms"]),
+            "call": "pinned H2D copy, gvom_update_extract, one D2H copy of the packed products, per step"}
+
+
+def plain_summary(args, r, workload, red_peak, hbm_peak, peak_kind):
+    """The sub-object of a plain workload measured beside the main leg."""
+    cfg = r["cfg"]
+    ms = cfg.map
+    steps = args.steps
+    return {"workload": workload_text(workload, r["n_scans"]), "metric": metric_of(workload),
+            "value": r["rays"] / r["total_s"], "unit": UNIT, "map_updates_per_s": steps / r["total_s"],
+            "ms_per_step_mean": 1e3 * r["total_s"] / steps, "ms_per_step_median": statistics.median(r["step_ms"]),
+            "rays_per_step": r["rays"] / steps, "pass_visits_per_step": r["visits"] / steps,
+            "hits_per_step": r["hits"] / steps, "shift_ms_mean": statistics.mean(r["shift_ms"]),
+            "ingest_ms_mean": statistics.mean(r["ingest_ms"]), "extract_ms_mean": statistics.mean(r["extract_ms"]),
+            "roofline": ingest_roofline(r, steps, red_peak, workload),
+            "roofline_step": roofline_step((r["visits"] + 2 * r["hits"]) / steps, red_peak, ms.nx * ms.ny * ms.nz, ms,
+                                           cfg.lidar.n, hbm_peak, r["total_s"] / steps),
+            "roofline_extract": extract_roofline(r, ms, hbm_peak, peak_kind),
+            "e2e": e2e_object(r), "gpu_launches_per_step": r["launches"] / steps,
+            "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1],
+                       "march_blocks_per_sm": r["tuning"][2]},
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def oracle_plain_baseline(inputs, time_budget_s: float, workload: str):
+    """The oracle on the first scans of a plain workload (one thread)."""
     cfg, scans = inputs
-    res = run_oracle_steps(cfg, scans, len(scans), time_budget_s=time_budget_s)
+    res = run_oracle_steps(cfg, scans, len(scans) * 10, time_budget_s=time_budget_s)
     return {"value": sum(r for r, _ in res) / sum(t for _, t in res), "unit": UNIT, "cores": 1, "kind": "oracle",
             "host": host_cpu(),
-            "sample": f"first {len(res)} scans of the high-speed workload, shift + ingest + extract each, single thread"}
+            "sample": f"first {len(res)} scans of the {workload} workload, shift + ingest + extract each, "
+                      "single thread"}
+
+
+def served_pools(torch, robots, arrivals):
+    """scans[robot][k] for the server: the arrival's cast (pinned host
+    memory, shared by the arrivals of one span) with the arrival's pose."""
+    casts = {i: [torch.from_numpy(c.points).pin_memory() for c in r["casts"]] for i, r in enumerate(robots)}
+    pools = {i: {} for i in range(len(robots))}
+    for t, rid, k, c, T, veh in arrivals:
+        pools[rid][k] = dict(points=casts[rid][c], T_ws=T, vehicle_xyz=veh)
+    return pools
 
 
 def run_served(args, gv, torch, inputs):
-    """The served workload: real-time replay with continuous batching (latency),
-    then all requests at once (capacity), batched vs one plain update per scan."""
+    """The served workload: real-time replay with continuous batching and
+    per-scan admission (latency), the same stream offered 2-16 times faster
+    (latency against load), then all requests at once (capacity); beside
+    them one plain update per scan."""
     from paper_2109_13176_gb300.serve import Server
     robots, arrivals = inputs
     specs = {i: r["map"] for i, r in enumerate(robots)}
-    scans = {i: [dict(points=torch.from_numpy(s.points).pin_memory(), T_ws=s.T_ws, vehicle_xyz=s.vehicle_xyz)
-                 for s in r["scans"]] for i, r in enumerate(robots)}
-    max_pts = sum(max(int(s["points"].shape[0]) for s in scans[i]) for i in scans)
+    pools = served_pools(torch, robots, arrivals)
+    arr = [(t, rid, k) for t, rid, k, *_ in arrivals]
+    max_pts = sum(max(int(c.points.shape[0]) for c in r["casts"]) for r in robots)
 
-    def server():
-        return Server(specs, slots=2, max_batch_maps=len(robots), max_batch_points=max_pts, reserve_bytes=2 << 30)
+    def replay(stream, realtime=True, scale=1.0):
+        srv = Server(specs, slots=2, max_batch_maps=len(robots), max_batch_points=max_pts, reserve_bytes=2 << 30)
+        # the collector stays off during each replay, as in the main leg's timed region
+        gc.collect()
+        gc.disable()
+        try:
+            out = srv.run(stream, pools, realtime=realtime, time_scale=scale).summary()
+        finally:
+            gc.enable()
+            srv.close()
+        return out
 
-    # the collector stays off during each replay, as in the main leg's timed region
-    srv = server()
-    gc.collect()
-    gc.disable()
-    try:
-        rt = srv.run(arrivals, scans, realtime=True).summary()
-    finally:
-        gc.enable()
-    srv.close()
-    srv = server()
-    gc.collect()
-    gc.disable()
-    try:
-        sat = srv.run(arrivals, scans, realtime=False).summary()
-    finally:
-        gc.enable()
-    srv.close()
+    rt = replay(arr)
+    sweep = [dict(load=1.0, offered_scans_per_s=len(arr) / args.served_seconds, window_s=args.served_seconds,
+                  **{k: rt[k] for k in ("requests", "p50_ms", "p99_ms", "max_ms", "mean_batch_maps", "rays_per_s",
+                                        "deferred")})]
+    for f in SERVED_LOADS:
+        # the first f * window seconds of the stream, offered f times faster
+        part = [a for a in arr if a[0] < f * SERVED_SWEEP_WINDOW_S]
+        st = replay(part, scale=f)
+        sweep.append(dict(load=f, offered_scans_per_s=f * len(arr) / args.served_seconds,
+                          window_s=min(SERVED_SWEEP_WINDOW_S, args.served_seconds / f),
+                          **{k: st[k] for k in ("requests", "p50_ms", "p99_ms", "max_ms", "mean_batch_maps",
+                                                "rays_per_s", "deferred")}))
+    ok = [p["load"] for p in sweep if p["p99_ms"] is not None and p["p99_ms"] < 100.0]
+    sat = replay(arr, realtime=False)
     # the plain path on the same requests: one update + extraction + readback per scan, in order
     maps = {i: gv.VoxelMap(nx=sp.nx, ny=sp.ny, nz=sp.nz, res=sp.res, neg_max_px=int(math.ceil(2.0 / sp.res)))
             for i, sp in specs.items()}
     outs = {i: m.alloc_maps() for i, m in maps.items()}
     host = {i: {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in o.items()} for i, o in outs.items()}
-    staging = torch.empty((max(int(s["points"].shape[0]) for i in scans for s in scans[i]), 3), device="cuda")
+    staging = torch.empty((max(int(c.points.shape[0]) for r in robots for c in r["casts"]), 3), device="cuda")
     r0 = {i: m.stats()["rays_valid"] for i, m in maps.items()}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for t, rid, k in arrivals:
-        sc = scans[rid][k]
+    for t, rid, k in arr:
+        sc = pools[rid][k]
         n = int(sc["points"].shape[0])
         view = staging[:n]
         view.copy_(sc["points"], non_blocking=True)
@@ -731,10 +842,14 @@ def run_served(args, gv, torch, inputs):
     for m in maps.values():
         m.close()
     return {"workload": SERVED_WORKLOAD.format(s=args.served_seconds), "robots": len(robots),
-            "requests": len(arrivals), "realtime": rt, "saturated": sat,
+            "requests": len(arr), "realtime": rt, "load_sweep": sweep,
+            "max_load_with_p99_under_100ms": max(ok) if ok else None,
+            "saturated": sat,
             "plain_sequential": {"rays_per_s": plain_rays / plain_s, "wall_s": plain_s},
             "capacity_speedup_vs_plain": sat["rays_per_s"] / (plain_rays / plain_s),
-            "slots": 2, "latency": "arrival to 2D products in pinned host memory (device event times)"}
+            "slots": 2, "admission": "per scan, device-memory budget (free memory at start - 2 GiB - staging); "
+                                     "maps created on a robot's first scan",
+            "latency": "arrival to 2D products in pinned host memory (device event times)"}
 
 
 def main():
@@ -744,16 +859,17 @@ def main():
         run_reference(args, rank, world)
         return
 
-    # inputs first: the generator's process pool starts before any CUDA call
-    cfg, scans = make_inputs(rank, args.workload, args.high_speed_scans)
-    hs_main = args.workload == "high_speed"
-    metric = METRIC_HIGH_SPEED if hs_main else METRIC
-    workload = HIGH_SPEED_WORKLOAD.format(n=len(scans)) if hs_main else WORKLOAD
+    # inputs first: the generator's process pools start before any CUDA call
+    main_wl = args.workload
+    other_wl = "sequence" if main_wl == "high_speed" else "high_speed"
+    inputs = make_inputs(rank, main_wl, args.high_speed_scans)
+    other_inputs = None if args.no_other else make_inputs(rank, other_wl, args.high_speed_scans)
+    seq_inputs = inputs if main_wl == "sequence" else other_inputs
+    if seq_inputs is None and not args.no_next_rows:
+        seq_inputs = make_inputs(rank, "sequence")
     batched_inputs = None if args.no_batched else make_batched_inputs(rank, args.batched_maps)
     served_inputs = None if args.no_served else make_served_inputs(rank, args.served_seconds)
-    hs_inputs = None if (args.no_high_speed or hs_main) else make_high_speed_inputs(rank, args.high_speed_scans)
 
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -765,93 +881,19 @@ def main():
     import paper_2109_13176_gb300 as gv
     from paper_2109_13176_gb300 import tune
 
-    ms = cfg.map
-    dev_pts = [torch.from_numpy(s.points).cuda() for s in scans]
-    host_pts = [torch.from_numpy(s.points).pin_memory() for s in scans]
-    gmap = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
-    out = gmap.alloc_maps()
     flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-
-    def step(k, ev_shift=None, ev_ingest=None):
-        s = scans[k % len(scans)]
-        gmap.shift(gmap.origin_for_pose(s.vehicle_xyz))
-        if ev_shift is not None:
-            ev_shift.record(stream)
-        gmap.ingest(dev_pts[k % len(scans)], s.T_ws)
-        if ev_ingest is not None:
-            ev_ingest.record(stream)
-        gmap.extract_maps(out)
+    flush_k = [0]
 
     def flush():
-        flush_buf.fill_(7)
+        flush_k[0] += 1
+        flush_buf.fill_(flush_k[0] & 0xff)
 
-    # launch shape for this workload: cached, or searched on its first scans
-    tuning, tune_entry = tune.tune_map(gmap, dev_pts[:4], [s.T_ws for s in scans[:4]],
-                                       [s.vehicle_xyz for s in scans[:4]], flush=flush, refresh=args.retune)
-    gmap.reset((0, 0, 0))
-    gmap.reset_stats()
-
-    for k in range(args.warmup):
-        step(k)
-    torch.cuda.synchronize()
-    st0 = gmap.stats()
-    n_ev = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(n_ev)]
-    launches0 = gv.gvom_kernel_launches()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    gc.collect()
-    gc.disable()
-    with ClockSampler(local) as clocks:
-        for i in range(args.steps):
-            flush_buf.fill_(i & 0xff)
-            e = ev[i]
-            e[0].record(stream)
-            step(args.warmup + i, e[1], e[2])
-            e[3].record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = gv.gvom_kernel_launches() - launches0  # this library's kernels only
-    st1 = gmap.stats()
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    ingest_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    extract_ms = [e[2].elapsed_time(e[3]) for e in ev]
-    total_s = sum(step_ms) * 1e-3
-    rays = st1["rays_valid"] - st0["rays_valid"]
-    visits = st1["pass_visits"] - st0["pass_visits"]
-    hits = st1["hits_in_window"] - st0["hits_in_window"]
-
-    # e2e through the public API with host buffers: pinned H2D of the scan,
-    # the update, and D2H of every 2D product, inside the timed region.
-    h2d = sum(p.numel() * 4 for p in host_pts) / len(host_pts)
-    # the products in one device buffer, read back with one copy
-    packed_dev, packed_out = gmap.alloc_maps_packed()
-    packed_host = torch.empty(packed_dev.numel(), dtype=torch.uint8, pin_memory=True)
-    d2h = packed_dev.numel()
-    staging = torch.empty_like(dev_pts[0])
-    e2e_ms = []
-    e2e_steps = max(args.steps, 200)  # host-sensitive: a longer window
-    for i in range(e2e_steps):
-        flush_buf.fill_(i & 0xff)
-        k = args.warmup + args.steps + i
-        s = scans[k % len(scans)]
-        hp = host_pts[k % len(scans)]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        staging.copy_(hp, non_blocking=True)
-        gmap.update_extract(s.vehicle_xyz, staging, s.T_ws, packed_out)
-        packed_host.copy_(packed_dev, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    gc.enable()
-    st2 = gmap.stats()
-    rays_e2e = st2["rays_valid"] - st1["rays_valid"]
-    e2e_s = sum(e2e_ms) * 1e-3
-
+    # the main leg: timed steps with clocks sampled, then e2e
+    clocks = ClockSampler(local)
+    r = measure_plain(args, gv, tune, torch, inputs, flush, stream, world=world, clocks=clocks,
+                      e2e_steps=max(args.steps, 200))
+    total_s, e2e_s, rays, rays_e2e = r["total_s"], r["e2e_s"], r["rays"], r["rays_e2e"]
     if world > 1:
         (total_s, e2e_s), (rays, rays_e2e) = reduce_over_ranks([total_s, e2e_s], [rays, rays_e2e], "cuda")
 
@@ -859,6 +901,18 @@ def main():
         dist.destroy_process_group() if world > 1 else None
         return
 
+    peaks, peak_kind = read_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    red_peak = measure_red_peak(gv, torch)
+    cfg = r["cfg"]
+    ms = cfg.map
+
+    other = None
+    if other_inputs is not None:
+        ro = measure_plain(args, gv, tune, torch, other_inputs, flush, stream)
+        other = plain_summary(args, ro, other_wl, red_peak, hbm_peak, peak_kind)
+        if not args.no_cpu_baseline:
+            other["cpu_baseline"] = oracle_plain_baseline(other_inputs, 6.0, other_wl)
     batched = None
     if batched_inputs is not None:
         batched = run_batched(args, gv, tune, torch, batched_inputs, flush, stream)
@@ -869,74 +923,52 @@ def main():
         served = run_served(args, gv, torch, served_inputs)
         if not args.no_cpu_baseline:
             served["cpu_baseline"] = oracle_served_baseline(served_inputs, 8.0)
-
-    peaks, peak_kind = read_peaks()
     next_rows = None
     if not args.no_next_rows:
-        next_rows = run_next_rows(args, gv, torch, cfg, scans, dev_pts, host_pts, tuning, flush, stream,
-                                  rays_e2e / e2e_s, peaks.get("hbm_gbs"))
-    high_speed = None
-    if hs_inputs is not None:
-        high_speed = run_high_speed(args, gv, tune, torch, hs_inputs, flush, stream, peaks.get("hbm_gbs"))
-        if not args.no_cpu_baseline:
-            high_speed["cpu_baseline"] = oracle_high_speed_baseline(hs_inputs, 6.0)
-    red_peak = measure_red_peak(gv, torch)
-    ingest_avg_s = statistics.mean(ingest_ms) * 1e-3
-    atom_per_launch = (visits + 2 * hits) / args.steps
-    achieved = atom_per_launch / ingest_avg_s
-    V = ms.nx * ms.ny * ms.nz
-    extract_bytes = 12 * V + (4 + 4 + 1 + 4 + 4) * ms.nx * ms.ny
-    extract_avg_s = statistics.mean(extract_ms) * 1e-3
+        seq_cfg, seq_scans = seq_inputs
+        seq_tuning = r["tuning"] if main_wl == "sequence" else (
+            tuple(other["tuning"].values()) if other else (16, 256, 0))
+        seq_e2e = (rays_e2e / e2e_s) if main_wl == "sequence" else (other["e2e"]["value"] if other else None)
+        next_rows = run_next_rows(args, gv, torch, seq_cfg, seq_scans, seq_tuning, flush, stream, seq_e2e, hbm_peak)
 
     cpu = None
     if not args.no_cpu_baseline:
-        res = run_oracle_steps(cfg, scans, len(scans) * 10, time_budget_s=args.cpu_sample_s)
-        cr = sum(r for r, _ in res)
-        cs = sum(t for _, t in res)
-        cpu = {"value": cr / cs, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-               "sample": f"first {len(res)} scans of the workload, shift + ingest + extract each, single thread"}
+        cpu = oracle_plain_baseline(inputs, args.cpu_sample_s, main_wl)
 
+    steps = args.steps
+    atom_per_launch = (r["visits"] + 2 * r["hits"]) / steps
     line = {
-        "metric": metric, "value": rays / total_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "metric": metric_of(main_wl), "value": rays / total_s, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 transform, int32 traversal, u32 counts, f32 maps",
         "data": f"synthetic (seeded procedural terrain, boxes, ditches; {cfg.lidar.beams}-beam lidar model)",
-        "config": {"workload": workload, "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
-                   "points_per_scan": cfg.lidar.n, "scans": len(scans),
+        "config": {"workload": workload_text(main_wl, r["n_scans"]), "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
+                   "points_per_scan": cfg.lidar.n, "scans": r["n_scans"],
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (one map per GPU)"},
-        "map_updates_per_s": args.steps * world / total_s,
-        "rays_per_step": rays / (args.steps * world),
-        "pass_visits_per_step": visits / args.steps,
-        "step_ms": {"median": statistics.median(step_ms), "p99": sorted(step_ms)[int(0.99 * (len(step_ms) - 1))],
-                    "ingest_avg": 1e3 * ingest_avg_s, "extract_avg": 1e3 * extract_avg_s},
-        "roofline": {"kernel": "k_ingest", "bound": "l2_atomic", "achieved": achieved / 1e9,
-                     "peak": red_peak / 1e9, "unit": "Gatomic/s", "frac": achieved / red_peak,
-                     "traffic": profile_traffic("k_ingest", "plain_high_speed" if hs_main else "plain_sequence"),
-                     "peak_source": "measured in this run: scattered 32-bit reduction atomics over 64 MiB (gvom_microbench_red)",
-                     "algorithmic": "pass visits + 2 atomics per in-window hit, per launch"},
-        "roofline_step": roofline_step(atom_per_launch, red_peak, V, ms, cfg.lidar.n, peaks.get("hbm_gbs"),
-                                      total_s / args.steps),
-        "roofline_extract": {"kernels": "k_columns + k_slope_negative", "bound": "hbm",
-                             "achieved": extract_bytes / extract_avg_s / 1e9, "peak": peaks.get("hbm_gbs"),
-                             "unit": "GB/s", "frac": extract_bytes / extract_avg_s / 1e9 / peaks.get("hbm_gbs"),
-                             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+        "map_updates_per_s": steps * world / total_s,
+        "rays_per_step": rays / (steps * world),
+        "pass_visits_per_step": r["visits"] / steps,
+        "step_ms": {"median": statistics.median(r["step_ms"]),
+                    "p99": sorted(r["step_ms"])[int(0.99 * (len(r["step_ms"]) - 1))],
+                    "shift_avg": statistics.mean(r["shift_ms"]), "ingest_avg": statistics.mean(r["ingest_ms"]),
+                    "extract_avg": statistics.mean(r["extract_ms"])},
+        "roofline": ingest_roofline(r, steps, red_peak, main_wl),
+        "roofline_step": roofline_step(atom_per_launch, red_peak, ms.nx * ms.ny * ms.nz, ms, cfg.lidar.n, hbm_peak,
+                                      r["total_s"] / steps),
+        "roofline_extract": extract_roofline(r, ms, hbm_peak, peak_kind),
         "cpu_baseline": cpu,
-        "e2e": {"value": rays_e2e / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step_p50": statistics.median(e2e_ms),
-                "ms_per_step_p99": sorted(e2e_ms)[int(0.99 * (len(e2e_ms) - 1))],
-                "call": "pinned H2D copy, gvom_update_extract, one D2H copy of the packed products, per step"},
-        "gpu_launches": int(launches),
+        "e2e": dict(e2e_object(r), value=rays_e2e / e2e_s),
+        "gpu_launches": int(r["launches"]),
         "clocks": clocks.summary(),
-        "tuning": {"seg_len": tuning[0], "march_block": tuning[1], "march_blocks_per_sm": tuning[2],
-                   "search_us": tune_entry.get("us")},
+        "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1], "march_blocks_per_sm": r["tuning"][2],
+                   "search_us": r["tune_entry"].get("us")},
+        other_wl: other,
         "batched": batched,
         "served": served,
         "next_rows": next_rows,
-        "high_speed": high_speed,
     }
     print(json.dumps(line), flush=True)
-    gmap.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -20,7 +20,7 @@ from .scenes import (  # noqa: F401
     sequence_config,
     sequence_scans,
     batched_scans,
-    served_requests,
+    served_stream,
     WORKLOADS,
     SEED_BASE,
     SEEDS,

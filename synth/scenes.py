@@ -23,10 +23,14 @@ batched: 64 maps of the sequence kind, each with its own terrain and
    continues at the edge height); each map's scan per step is a seeded
    random subset (scan order kept) of a 128 x 2048 scan, of size
    floor(exp U(ln 8192, ln 262144)).
-served: 32 robots with mixed sensors (16/64/128 beams) and maps, arrivals
-   with exponential inter-arrival times (mean 100 ms), over a stream of
-   given length; each robot draws its scans from a small pool of consecutive
-   scans of its own trajectory.
+served: 32 robots with mixed sensors (16/64/128 beams) and maps, each with
+   its own seeded speed (2-12 m/s) and route (features lining it at the
+   sequence workload's density), arrivals with exponential inter-arrival
+   times (mean 100 ms) over the stream. Every arrival carries the pose of
+   the robot's trajectory at its arrival time (the window moves forward
+   with the robot); its points come from one of 8 lidar casts per robot,
+   cast at the middle of 8 equal spans of the stream and used for the
+   arrivals of that span (sensor frame, re-posed).
 Every scan: range noise N(0, 0.02 m) along the beam; beams with no return
 within 120 m report the zero point (which the map update drops, as it drops
 returns beyond its 100 m range).
@@ -149,9 +153,35 @@ class Scene:
         xs = x0 + g * np.arange(nxr)
         ys = y0 + g * np.arange(nyr)
         H = np.empty((nxr, nyr), dtype=np.float32)
-        for i in range(0, nxr, 256):
-            X, Y = np.meshgrid(xs[i:i + 256], ys, indexing="ij")
-            H[i:i + 256] = self.ground_exact(X, Y)
+        # the smooth part over the whole raster, then each ditch over the
+        # raster cells of its bounding square only
+        all_ditches = self.ditches
+        self.ditches = []
+        try:
+            for i in range(0, nxr, 256):
+                X, Y = np.meshgrid(xs[i:i + 256], ys, indexing="ij")
+                H[i:i + 256] = self.ground_exact(X, Y)
+        finally:
+            self.ditches = all_ditches
+        # each ditch's square is recomputed whole (smooth part and every ditch
+        # that reaches the square, in list order), so the raster equals
+        # ground_exact everywhere
+        def square(d):
+            r = d.hl + d.hw
+            return (max(0, math.floor((d.cx - r - x0) / g)), min(nxr, math.floor((d.cx + r - x0) / g) + 2),
+                    max(0, math.floor((d.cy - r - y0) / g)), min(nyr, math.floor((d.cy + r - y0) / g) + 2))
+        squares = [square(d) for d in all_ditches]
+        for i0, i1, j0, j1 in squares:
+            if i0 >= i1 or j0 >= j1:
+                continue
+            near = [d for d, (a0, a1, b0, b1) in zip(all_ditches, squares)
+                    if a0 < i1 and i0 < a1 and b0 < j1 and j0 < b1]
+            X, Y = np.meshgrid(xs[i0:i1], ys[j0:j1], indexing="ij")
+            self.ditches = near
+            try:
+                H[i0:i1, j0:j1] = self.ground_exact(X, Y)
+            finally:
+                self.ditches = all_ditches
         self._grid = (x0, y0, g, H)
 
     def ground(self, x: np.ndarray, y: np.ndarray) -> np.ndarray:
@@ -210,14 +240,39 @@ class Scene:
             f = fn[keep]
         return t_hit
 
-    def _cast_boxes(self, o: np.ndarray, d: np.ndarray) -> np.ndarray:
+    def _cast_boxes(self, o: np.ndarray, d: np.ndarray, reach: float = np.inf) -> np.ndarray:
         n = d.shape[0]
         best = np.full(n, np.inf)
+        # rays sorted by azimuth: a box can only be hit by the rays whose
+        # azimuth lies within the angle its bounding circle subtends
+        az = np.arctan2(d[:, 1], d[:, 0])
+        order = np.argsort(az, kind="stable")
+        az_sorted = az[order]
         for b in self.boxes:
+            rb = math.hypot(b.hx, b.hy)
+            dist = math.hypot(b.cx - o[0], b.cy - o[1])
+            if dist > reach + rb:
+                continue
+            if dist > rb + 1e-6:
+                half = math.asin(min(1.0, rb / dist)) + 1e-9
+                a0 = math.atan2(b.cy - o[1], b.cx - o[0])
+                lo_a, hi_a = a0 - half, a0 + half
+                idx = []
+                for lo, hi in ((lo_a, hi_a), (lo_a + 2 * math.pi, hi_a + 2 * math.pi),
+                               (lo_a - 2 * math.pi, hi_a - 2 * math.pi)):
+                    i0, i1 = np.searchsorted(az_sorted, [lo, hi])
+                    if i1 > i0:
+                        idx.append(order[i0:i1])
+                if not idx:
+                    continue
+                sel = np.concatenate(idx)
+            else:
+                sel = np.arange(n)
             c, s = math.cos(b.yaw), math.sin(b.yaw)
             ox, oy = o[0] - b.cx, o[1] - b.cy
             lo_ = np.array([c * ox + s * oy, -s * ox + c * oy, o[2]])
-            ld = np.stack([c * d[:, 0] + s * d[:, 1], -s * d[:, 0] + c * d[:, 1], d[:, 2]], axis=1)
+            ds = d[sel]
+            ld = np.stack([c * ds[:, 0] + s * ds[:, 1], -s * ds[:, 0] + c * ds[:, 1], ds[:, 2]], axis=1)
             bmin = np.array([-b.hx, -b.hy, b.z0])
             bmax = np.array([b.hx, b.hy, b.z1])
             with np.errstate(divide="ignore", invalid="ignore"):
@@ -227,13 +282,16 @@ class Scene:
             tmin = np.nanmax(np.minimum(t1, t2), axis=1)
             tmax = np.nanmin(np.maximum(t1, t2), axis=1)
             ok = (tmax >= tmin) & (tmin > 1e-6)
-            best = np.where(ok & (tmin < best), tmin, best)
+            cur = best[sel]
+            best[sel] = np.where(ok & (tmin < cur), tmin, cur)
         return best
 
-    def _cast_veg(self, o, d, t_hit, rng) -> np.ndarray:
+    def _cast_veg(self, o, d, t_hit, rng, reach: float = np.inf) -> np.ndarray:
         out = t_hit.copy()
         for v in self.veg:
             ox, oy = o[0] - v.cx, o[1] - v.cy
+            if math.hypot(ox, oy) > reach + v.radius:
+                continue
             a = d[:, 0] ** 2 + d[:, 1] ** 2
             bq = 2.0 * (ox * d[:, 0] + oy * d[:, 1])
             cq = ox * ox + oy * oy - v.radius ** 2
@@ -260,11 +318,11 @@ class Scene:
     def cast(self, o: np.ndarray, d: np.ndarray, t_max: float, rng) -> np.ndarray:
         """First-return range of each unit ray from o (world frame); NaN if none."""
         tg = self._cast_ground(o, d, t_max)
-        tb = self._cast_boxes(o, d)
+        tb = self._cast_boxes(o, d, t_max)
         t = np.fmin(tg, tb)
         t = np.where(np.isinf(t), np.nan, t)
         if self.veg:
-            t = self._cast_veg(o, d, np.where(np.isnan(t), np.inf, t), rng)
+            t = self._cast_veg(o, d, np.where(np.isnan(t), np.inf, t), rng, t_max)
             t = np.where(np.isinf(t), np.nan, t)
         t = np.where(t <= t_max, t, np.nan)
         return t
@@ -509,35 +567,67 @@ SERVED_MAPS = (MapSpec(128, 128, 32, 0.2), MapSpec(256, 256, 64, 0.2), MapSpec(5
 SERVED_LIDARS = (LidarSpec(16, 1024, 15.0), LidarSpec(64, 2048, 16.6), LidarSpec(128, 2048, 22.5))
 
 
+SERVED_CASTS = 8  # lidar casts per robot, spread over its stream
+
+
 def _served_robot(args):
-    """Map spec, lidar and scan pool of one served robot."""
-    seed, i, pool = args
+    """One served robot: its map and sensor, its own trajectory over the
+    whole stream (speed and route seeded per robot), its arrivals, and the
+    lidar casts that give each arrival its points."""
+    seed, i, duration_s, casts, rate_hz = args
     r = np.random.default_rng([seed, 0, i])
     ms = SERVED_MAPS[int(r.integers(0, 3))]
     ld = SERVED_LIDARS[int(r.integers(0, 3))]
     speed = float(r.uniform(2.0, 12.0))
-    cfg = SequenceConfig(ms, ld, pool, speed, rough=0.1 if ms.res < 0.2 else 0.0)
-    yaw0 = float(r.uniform(0, 2 * np.pi))
-    sc = make_sequence_scene(cfg, r, yaw0=yaw0, extent=70.0)
-    scans = []
-    for k in range(pool):
-        t = k / 10.0
-        veh, yaw, pitch = _trajectory_pose(sc, speed, t, yaw0=yaw0)
+    rough = 0.1 if ms.res < 0.2 else 0.0
+    # the robot's route is speed * duration metres long; features line it
+    # with the density of the sequence workload (30 boxes, 10 ditches per
+    # 60 m x 50 m)
+    route = speed * duration_s
+    area = (route + 50.0) * 50.0
+    sc = random_scene(r, (-25.0, route + 25.0), (-25.0, 25.0), rough=rough,
+                      veg_clusters=int(round(area / 1500.0)) if rough > 0 else 0,
+                      n_boxes=int(round(30 * area / 3000.0)), n_ditches=int(round(10 * area / 3000.0)),
+                      raster=0.2, path=lambda x: float(_path_y(x)))
+    # arrivals: exponential inter-arrival times with mean 1 / rate_hz
+    ra = np.random.default_rng([seed, 2, i])
+    times = []
+    t = float(ra.uniform(0, 1.0 / rate_hz))
+    while t < duration_s:
+        times.append(t)
+        t += float(ra.exponential(1.0 / rate_hz))
+    # casts at the middle of equal spans of the stream; an arrival takes the
+    # cast of its span, re-posed to its own pose on the trajectory
+    span = duration_s / casts
+    cast_scans = []
+    for j in range(casts):
+        tc = (j + 0.5) * span
+        veh, yaw, pitch = _trajectory_pose(sc, speed, tc)
+        sc.build_raster(veh[0] - ld.max_cast - 2.0, veh[0] + ld.max_cast + 2.0,
+                        veh[1] - ld.max_cast - 2.0, veh[1] + ld.max_cast + 2.0)
         T = pose_matrix(veh, yaw, pitch)
-        scans.append(scan_from_pose(sc, ld, T, veh, np.random.default_rng([seed, 1, i, k]), t=t))
-    return dict(map=ms, lidar=ld, scans=scans)
+        cast_scans.append(scan_from_pose(sc, ld, T, veh, np.random.default_rng([seed, 1, i, j]), t=tc))
+        sc._grid = None
+    arrivals = []
+    for k, t in enumerate(times):
+        veh, yaw, pitch = _trajectory_pose(sc, speed, t)
+        arrivals.append((t, k, min(casts - 1, int(t / span)), pose_matrix(veh, yaw, pitch), veh))
+    return dict(map=ms, lidar=ld, speed=speed, casts=cast_scans, arrivals=arrivals)
 
 
-def served_requests(n_robots: int = 32, duration_s: float = 60.0, pool: int = 4,
-                    seed: int | None = None, workers: int = 0):
-    """Robots (map spec, scan pool) and a time-ordered arrival list (the served workload).
+def served_stream(n_robots: int = 32, duration_s: float = 60.0, casts: int = SERVED_CASTS, rate_hz: float = 10.0,
+                  seed: int | None = None, workers: int = 0):
+    """The served workload: robots with their maps, sensors and trajectories,
+    and the time-ordered arrivals of all robots.
 
-    Returns (robots, arrivals): robots[i] = dict(map=MapSpec, lidar=LidarSpec,
-    scans=[Scan]*pool); arrivals = list of (t_arrival_s, robot, pool_index).
-    Robot i cycles through its pool of consecutive scans. workers > 1 builds
+    Returns (robots, arrivals). robots[i] = dict(map=MapSpec, lidar=LidarSpec,
+    speed=m/s, casts=[Scan] * casts). arrivals = list of (t_s, robot, k,
+    cast, T_ws, vehicle_xyz), sorted by t: robot's k-th scan arrives at t_s
+    with the pose of its own trajectory at that time; its points are
+    robots[robot]["casts"][cast].points (sensor frame). workers > 1 builds
     robots in a spawn-started process pool (same result)."""
     seed = SEEDS["served"] if seed is None else seed
-    jobs = [(seed, i, pool) for i in range(n_robots)]
+    jobs = [(seed, i, duration_s, casts, rate_hz) for i in range(n_robots)]
     if workers and workers > 1:
         import multiprocessing as mp
         from concurrent.futures import ProcessPoolExecutor
@@ -546,15 +636,10 @@ def served_requests(n_robots: int = 32, duration_s: float = 60.0, pool: int = 4,
     else:
         robots = [_served_robot(j) for j in jobs]
     arr = []
-    r = np.random.default_rng([seed, 2])
-    for i in range(n_robots):
-        t = float(r.uniform(0, 0.1))
-        k = 0
-        while t < duration_s:
-            arr.append((t, i, k % pool))
-            k += 1
-            t += float(r.exponential(0.1))
-    arr.sort()
+    for i, rb in enumerate(robots):
+        for t, k, c, T, veh in rb.pop("arrivals"):
+            arr.append((t, i, k, c, T, veh))
+    arr.sort(key=lambda a: (a[0], a[1]))
     return robots, arr
 
 

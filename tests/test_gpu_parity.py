@@ -85,7 +85,7 @@ def compare_stats(gm, om):
     assert st["points_in"] == om.stats.points_in
 
 
-def run_sequence(gv, params, scans, stride=3, check_each=True):
+def run_sequence(gv, params, scans, stride=3, check_each=True, products_each=False):
     om = oracle.OracleMap(params)
     gm = gv.VoxelMap(gpu_config(gv, params))
     for s in scans:
@@ -98,7 +98,14 @@ def run_sequence(gv, params, scans, stride=3, check_each=True):
         gm.update(s.vehicle_xyz, to_dev(pts), s.T_ws)
         if check_each:
             compare_voxels(gm, om)
+        if products_each:
+            compare_products(gm, om)
     return gm, om
+
+
+def gen_workers():
+    import os
+    return max(1, min(16, (os.cpu_count() or 2) - 1))
 
 
 def test_single_scan(gv):
@@ -117,22 +124,24 @@ def test_single_scan_stride4(gv):
     compare_products(gm, om)
 
 
-def test_sequence_first_scans(gv):
-    # the 256 x 256 x 64 map, shifting every scan, at full size
-    cfg, scans = synth.sequence_scans("sequence", n_scans=4)
+def test_sequence_all_scans(gv):
+    # the sequence workload as the benchmark times it: all 20 scans into the
+    # 256 x 256 x 64 map, shifting every scan; state and every product after
+    # each scan
+    cfg, scans = synth.sequence_scans("sequence", workers=gen_workers())
+    assert len(scans) == 20
     params = params_for(cfg.map)
-    gm, om = run_sequence(gv, params, scans)
+    gm, om = run_sequence(gv, params, scans, products_each=True)
     compare_stats(gm, om)
-    compare_products(gm, om)
 
 
 def test_high_speed_scans_full_size(gv):
-    # the 512 x 512 x 64 map at 0.1 m: two consecutive scans (12 voxels apart)
-    cfg, scans = synth.sequence_scans("high_speed", n_scans=2, stride=1)
+    # the 512 x 512 x 64 map at 0.1 m: the workload's first 10 consecutive
+    # scans (12 voxels apart), state and every product after each
+    cfg, scans = synth.sequence_scans("high_speed", n_scans=10, stride=1, workers=gen_workers())
     params = params_for(cfg.map)
-    gm, om = run_sequence(gv, params, scans)
+    gm, om = run_sequence(gv, params, scans, products_each=True)
     compare_stats(gm, om)
-    compare_products(gm, om)
 
 
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 255, 257, 1000, 4099])

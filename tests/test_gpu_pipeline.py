@@ -23,7 +23,9 @@ def gv():
     return m
 
 
-def run_both(gv, kw, scans, max_points):
+def run_both(gv, kw, scans, max_points, om=None):
+    """Pipeline against the plain path, scan by scan; with an oracle map om,
+    each scan's products are also compared with the oracle's."""
     plain = gv.VoxelMap(**kw)
     piped = gv.VoxelMap(**kw)
     pipe = gv.Pipeline(piped, max_points)
@@ -43,6 +45,10 @@ def run_both(gv, kw, scans, max_points):
         torch.cuda.synchronize()
         for k in ref:
             np.testing.assert_array_equal(o[k].numpy(), ref[k].cpu().numpy(), err_msg=k)
+        if om is not None:
+            om.shift_for_pose(s["vehicle_xyz"])
+            om.ingest(s["points"], s["T_ws"])
+            oracle_products_match({k: v.numpy() for k, v in o.items()}, om.extract())
     for x, y in zip(plain.extract_voxels(), piped.extract_voxels()):
         np.testing.assert_array_equal(x.cpu().numpy(), y.cpu().numpy())
     pipe.close()
@@ -50,12 +56,30 @@ def run_both(gv, kw, scans, max_points):
     piped.close()
 
 
+def oracle_products_match(out, ref):
+    """The tolerances of the parity tests: height, flags bit-exact, density
+    1e-6 relative, slope 1e-3 rad, roughness 1e-4 m^2, same defined pixels."""
+    np.testing.assert_array_equal(out["height"], ref["height"])
+    np.testing.assert_array_equal(out["flags"], ref["flags"])
+    np.testing.assert_allclose(out["density"], ref["density"], rtol=1e-6, atol=0)
+    for k, tol in (("slope", 1e-3), ("roughness", 1e-4)):
+        np.testing.assert_array_equal(np.isnan(out[k]), np.isnan(ref[k]), err_msg=k)
+        m = ~np.isnan(ref[k])
+        if m.any():
+            assert np.max(np.abs(out[k][m] - ref[k][m])) <= tol, k
+
+
 def test_pipeline_full_size_sequence(gv):
+    # five scans of the sequence workload in flight through the pipeline:
+    # each scan's host products equal the plain path's and the oracle's
+    import oracle
     cfg, scans = synth.sequence_scans("sequence", n_scans=5)
     ms = cfg.map
     kw = dict(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res, neg_max_px=int(math.ceil(2.0 / ms.res)))
     seq = [dict(points=s.points, T_ws=s.T_ws, vehicle_xyz=s.vehicle_xyz) for s in scans]
-    run_both(gv, kw, seq, max(len(s.points) for s in scans))
+    om = oracle.OracleMap(oracle.OracleParams(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res,
+                                              neg_max_px=int(math.ceil(2.0 / ms.res))))
+    run_both(gv, kw, seq, max(len(s.points) for s in scans), om=om)
 
 
 @pytest.mark.parametrize("K", [0, 2])

@@ -84,12 +84,48 @@ def test_served_results_equal_solo(gv, realtime):
     srv.close()
 
 
-def test_admission_refuses_robots_beyond_memory(gv):
+def test_admission_by_memory_waits_and_retries(gv):
+    # a budget that holds one map at a time: robot 1's scans wait for memory
+    # until robot 0 has been idle for 50 ms and gives its map back; then
+    # robot 1 is admitted and its scans run in order. Each robot's results
+    # equal its scans applied alone.
     from paper_2109_13176_gb300.serve import Server, map_bytes
+    rng = np.random.default_rng(3)
     specs = {0: SPECS[0], 1: SPECS[1]}
-    free = [map_bytes(SPECS[0]) + 1000]
-    srv = Server(specs, slots=1, max_batch_maps=2, max_batch_points=1000, reserve_bytes=0,
-                 mem_free_fn=lambda: free[0])
-    assert 0 in srv.maps and 1 not in srv.maps
-    assert srv.admission.refused == [1]
+    pools = {r: make_pool(rng, 4) for r in specs}
+    arrivals = [(0.00, 0, 0), (0.01, 1, 0), (0.02, 0, 1), (0.03, 1, 1), (0.04, 0, 2), (0.05, 1, 2),
+                (0.06, 0, 3), (0.07, 1, 3)]
+    budget = max(map_bytes(sp) for sp in specs.values()) + 1000
+    srv = Server(specs, slots=1, max_batch_maps=2, max_batch_points=20000, budget_bytes=budget, idle_release_s=0.05)
+    last = {}
+
+    def on_done(req):
+        last[req.robot] = {k: v.clone() for k, v in srv.host_outs[req.robot].items()}
+
+    st = srv.run(arrivals, pools, realtime=True, on_done=on_done).summary()
+    assert st["requests"] == len(arrivals) and st["unserved_scans"] == 0
+    assert st["refused_robots"] == [1] and st["waited_scans"] == 4 and st["released_maps"] >= 1
+    for r, spec in specs.items():
+        solo = gv.VoxelMap(nx=spec.nx, ny=spec.ny, nz=spec.nz, res=spec.res, neg_max_px=int(math.ceil(2.0 / spec.res)))
+        for k in range(4):
+            sc = pools[r][k]
+            solo.update(sc["vehicle_xyz"], sc["points"].cuda(), sc["T_ws"])
+        ref = {k: v.cpu() for k, v in solo.extract_maps().items()}
+        for k in ref:
+            np.testing.assert_array_equal(last[r][k].numpy(), ref[k].numpy(), err_msg=k)
+        solo.close()
+    assert 1 in srv.maps
+    srv.close()
+
+
+def test_oversized_scan_is_rejected_and_the_rest_served(gv):
+    from paper_2109_13176_gb300.serve import Server
+    rng = np.random.default_rng(4)
+    specs = {0: SPECS[0]}
+    pools = {0: make_pool(rng, 3)}
+    big = torch.zeros((30000, 3), dtype=torch.float32).pin_memory()
+    pools[0].append(dict(points=big, T_ws=pools[0][0]["T_ws"], vehicle_xyz=pools[0][0]["vehicle_xyz"]))
+    srv = Server(specs, slots=1, max_batch_maps=1, max_batch_points=20000, reserve_bytes=0)
+    st = srv.run([(0.0, 0, 0), (0.0, 0, 3), (0.0, 0, 1), (0.0, 0, 2)], pools, realtime=False).summary()
+    assert st["rejected_scans"] == 1 and st["requests"] == 3
     srv.close()

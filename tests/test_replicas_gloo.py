@@ -87,5 +87,5 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert line["config"]["map"] == [256, 256, 64]
+    assert line["config"]["map"] == [512, 512, 64]
     assert line["cpu_baseline"]["host"]["nproc"] >= 1 and line["cpu_baseline"]["host"]["model"]
