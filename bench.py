@@ -406,6 +406,7 @@ def run_reference(args, rank, world):
 def run_batched(args, gv, tune, torch, inputs, flush, stream):
     """The batched workload: the same maps and scans stepped as one batch
     (graph replay) and as one plain update + extraction per map."""
+    import numpy as np
     cfg4, steps = inputs
     ms = cfg4.map
     nm = len(steps[0])
@@ -463,6 +464,25 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
     b_rate, b_ms, b_l, b_rays = timed(batched_step, maps_b)
     # the two forms computed the same maps
     same = all(torch.equal(outs_b[i]["flags"], outs_p[i]["flags"]) for i in range(nm))
+    # fixed cost of the step's graph: the same maps, no points and no window
+    # motion, no extraction, so its kernels (shift, per-point pass, walk) find
+    # no work: what is left is launch and drain
+    empty = [torch.empty((0, 3), dtype=torch.float32, device="cuda") for _ in range(nm)]
+    # a vehicle position whose window origin is the map's current one
+    half = np.array([ms.nx // 2, ms.ny // 2, ms.nz // 2], dtype=np.float64)
+    veh0 = [(np.asarray(maps_b[i].origin, dtype=np.float64) + half + 0.5) * ms.res for i in range(nm)]
+    for _ in range(3):
+        batch.step(maps_b, veh0, empty, poses[0])
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.step(maps_b, veh0, empty, poses[0])
+        e1.record(stream)
+        e1.synchronize()
+        e_ms.append(e0.elapsed_time(e1))
+    empty_launches = 3
     batch.close()
     for m in maps_b + maps_p:
         m.close()
@@ -474,6 +494,12 @@ def run_batched(args, gv, tune, torch, inputs, flush, stream):
             "gpu_launches_per_step_batched": b_l, "gpu_launches_per_step_plain": p_l,
             "graph": True, "tuning": {"seg_len": best[0], "march_block": best[1], "march_blocks_per_sm": best[2]},
             "outputs_identical": bool(same), "steps": args.batched_steps,
+            "graph_fixed_cost": {"empty_step_us_median": 1e3 * statistics.median(e_ms), "kernels": empty_launches,
+                                 "per_kernel_us": 1e3 * statistics.median(e_ms) / empty_launches,
+                                 "share_of_step_for_all_kernels": (1e3 * statistics.median(e_ms) / empty_launches)
+                                 * b_l / (1e3 * b_ms),
+                                 "note": "graph replay of a step with no points, no window motion and no "
+                                         "extraction (shift, per-point pass and walk launch with nothing to do)"},
             "l2": "flushed between timed steps (256 MiB write)"}
 
 

@@ -97,7 +97,7 @@ struct gvom_batch {
     // captured graph and what it was captured for
     cudaGraphExec_t exec;
     cudaStream_t cap_stream;
-    int g_B, g_extract, g_slots, g_zmax;
+    int g_B, g_extract, g_slots, g_zmax, g_pow2;
     size_t g_px_smem;  // the captured pixel pass's shared memory per block
     long long g_cap_items;
     long long g_kernels;  // kernels in the captured graph, counted per replay
@@ -235,6 +235,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     long long total = 0, items = 0;
     size_t px_smem = 0;  // the pixel pass's shared memory: the largest any map of the step needs
     int zmax = 0;  // the largest nz, or -1 when some map cannot use the bulk-copy column pass
+    int pow2 = 1;  // every map's window has power-of-two extents (the walk steps its index)
     for (int m = 0; m < B; ++m) {
         const gvom_map* mp = maps[m];
         if (!mp || n[m] < 0 || (n[m] > 0 && !pts_dev[m])) return GVOM_ERR_INVALID_ARG;
@@ -250,6 +251,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         px_smem = pm > px_smem ? pm : px_smem;
         const int nz = mp->cfg.nz;
         if (zmax >= 0) zmax = ((nz & 3) == 0 && nz <= 256) ? (nz > zmax ? nz : zmax) : -1;
+        pow2 &= gvom::pow2_window(gvom::geom_of(mp)) ? 1 : 0;
     }
     if (total > b->max_points) return GVOM_ERR_INVALID_ARG;
     if (zmax < 0) zmax = 0;
@@ -352,20 +354,21 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     const int do_extract = outs != nullptr;
 
     if (!(b->flags & GVOM_BATCH_GRAPH)) {
-        e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, st);
+        e = gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, pow2, st);
         if (e == cudaSuccess && do_extract) e = gvom::launch_batch_extract(t, b->max_maps, px_smem, zmax, st);
         return gvom::cuda_status(e);
     }
 
     if (!b->exec || b->g_extract != do_extract || b->g_px_smem < px_smem || b->g_cap_items != b->w.cap_items ||
-        b->g_slots != slots || b->g_zmax != zmax) {
+        b->g_slots != slots || b->g_zmax != zmax || b->g_pow2 != pow2) {
         drop_graph(b);
         cudaGraph_t graph = nullptr;
         const long long before = gvom_kernel_launches();
         e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t le =
-                gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, b->cap_stream);
+                gvom::launch_batch_update(t, b->max_maps, max_ray_blocks, shared, shape, slots, slots, pow2,
+                                          b->cap_stream);
             if (le == cudaSuccess && do_extract)
                 le = gvom::launch_batch_extract(t, b->max_maps, px_smem, zmax, b->cap_stream);
             e = cudaStreamEndCapture(b->cap_stream, &graph);
@@ -382,6 +385,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         b->g_px_smem = px_smem;
         b->g_zmax = zmax;
         b->g_slots = slots;
+        b->g_pow2 = pow2;
         b->g_cap_items = b->w.cap_items;
         b->g_kernels = gvom_kernel_launches() - before;
         gvom::count_launch(-b->g_kernels);  // captured, not launched
@@ -478,7 +482,7 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
     shape.blocks_per_sm = mp->tune.march_blocks_per_sm;
     const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
     return cuda_status(launch_batch_update(tables_at(b->d_tables, b->L), b->max_maps, max_ray_blocks, shared, shape,
-                                           evict != 0ull, buffered, st));
+                                           evict != 0ull, buffered, pow2_window(g), st));
 }
 
 }  // namespace gvom

@@ -165,8 +165,11 @@ long long tiles_of(const ExtractParams& p);
 int tile_halo(const ExtractParams& p);
 // evict: run the eviction kernel after the shifts; slots: some map of the
 // step writes a ring slot.
+// pow2: every map of the step has power-of-two extents.
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
-                                const MarchShape& shape, bool evict, bool slots, cudaStream_t st);
+                                const MarchShape& shape, bool evict, bool slots, bool pow2, cudaStream_t st);
+// Whether every extent of the window is a power of two.
+bool pow2_window(const Geom& g);
 long long evict_units(const MapState& s);
 // zmax > 0: every map's nz is a multiple of 4 and at most 256, zmax the
 // largest (the bulk-copy column pass); 0: the vector/scalar column pass.

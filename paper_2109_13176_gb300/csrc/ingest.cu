@@ -339,6 +339,15 @@ struct Walk {
     int rM, rA, rB;     // ring offsets
     int nM;
     uint32_t kM, kA, kB;  // strides of the state array per role
+    // Windows whose extents are all powers of two: the physical index of the
+    // current voxel is kept up to date instead of being recomputed. Axis k
+    // owns the bit field fm_k of the index (its extent's bits, at its
+    // stride), so a unit step is an add of st_k = +-stride_k kept within
+    // the field: the field wraps modulo the extent, which is exactly the
+    // toroidal addressing, and the other fields are untouched.
+    uint32_t key;
+    uint32_t fmM, fmA, fmB;
+    uint32_t stM, stA, stB;
 };
 
 __device__ __forceinline__ int rank_of(int dir) { return dir > 0 ? 0 : 1; }
@@ -429,6 +438,17 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     w.kM = sel3(st, M);
     w.kA = sel3(st, A);
     w.kB = sel3(st, B);
+    // power-of-two windows: the index fields (meaningful once the voxel is
+    // inside; the fields hold (c + r) mod n for any c, also before entry)
+    const uint32_t fm[3] = {((uint32_t)g.nx - 1u) * st[0], ((uint32_t)g.ny - 1u) * st[1], (uint32_t)g.nz - 1u};
+    w.fmM = sel3(fm, M);
+    w.fmA = sel3(fm, A);
+    w.fmB = sel3(fm, B);
+    w.stM = w.dirM > 0 ? w.kM : 0u - w.kM;
+    w.stA = w.dirA > 0 ? w.kA : 0u - w.kA;
+    w.stB = w.dirB > 0 ? w.kB : 0u - w.kB;
+    w.key = (((uint32_t)(w.cM + w.rM) * w.kM) & w.fmM) | (((uint32_t)(w.cA + w.rA) * w.kA) & w.fmA) |
+            (((uint32_t)(w.cB + w.rB) * w.kB) & w.fmB);
     return true;
 }
 
@@ -469,7 +489,9 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
     visits = 0;
 }
 
-template <bool kBatch, bool kSlot>
+// kPow2: every window of the launch has power-of-two extents (the index of
+// the current voxel is stepped, not recomputed).
+template <bool kBatch, bool kSlot, bool kPow2>
 __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
@@ -525,7 +547,7 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
         while (__any_sync(0xffffffffu, live)) {
             live = live && w.total != 0;
             const bool inside = live && (unsigned)w.cA < (unsigned)w.nA && (unsigned)w.cB < (unsigned)w.nB;
-            const uint32_t key = inside ? walk_index(w) : 0xffffffffu;
+            const uint32_t key = inside ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
             // runs of neighbouring lanes in the same voxel merge their
             // increments: the run's first lane adds the run's length
             bool boundary;
@@ -552,7 +574,12 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
             // the major step past the segment's last slab ends the segment
             live = live && !(gM && w.segM == 0);
             w.segM -= gM ? 1 : 0;
-            w.cM += gM ? w.dirM : 0;
+            if (kPow2) {
+                w.key = ((w.key + (gM ? w.stM : 0u)) & w.fmM) | ((w.key + (gA ? w.stA : 0u)) & w.fmA) |
+                        ((w.key + (gB ? w.stB : 0u)) & w.fmB);
+            } else {
+                w.cM += gM ? w.dirM : 0;
+            }
             w.cA += gA ? w.dirA : 0;
             w.cB += gB ? w.dirB : 0;
             w.dMA += (gM ? w.sA : 0) - (gA ? w.sM : 0);
@@ -876,7 +903,7 @@ __global__ void __launch_bounds__(256) k_evict_batch(BatchTables t) {
 }
 
 // Blocks of the persistent segment walk: every SM filled to its occupancy.
-template <bool kBatch, bool kSlot>
+template <bool kBatch, bool kSlot, bool kPow2>
 int march_grid(const MarchShape& shape) {
     int dev = 0, sms = 0, nb = 0;
     cudaGetDevice(&dev);
@@ -885,11 +912,11 @@ int march_grid(const MarchShape& shape) {
     int per_sm = shape.blocks_per_sm;
     if (per_sm <= 0) {
         // resident blocks per SM for 128- and 256-thread blocks, per device
-        static std::atomic<int> cache[64][2];
+        static std::atomic<int> cache[64][2];  // one per instantiation
         const int b = shape.block == 256 ? 1 : 0;
         nb = dev >= 0 && dev < 64 ? cache[dev][b].load(std::memory_order_relaxed) : 0;
         if (nb <= 0) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<kBatch, kSlot>, shape.block, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<kBatch, kSlot, kPow2>, shape.block, 0);
             if (nb > 0 && dev >= 0 && dev < 64) cache[dev][b].store(nb, std::memory_order_relaxed);
         }
         per_sm = nb > 0 ? nb : 1;
@@ -909,8 +936,16 @@ long long shift_units(const Geom& g, const int d[3], int whole) {
 
 long long evict_units(const MapState& s) { return ((long long)s.V + 1023) / 1024; }
 
+template <bool kSlot, bool kPow2>
+cudaError_t launch_march_batch(const BatchTables& t, const IngestArgs& shared, const MarchShape& shape,
+                               cudaStream_t st) {
+    k_march<true, kSlot, kPow2><<<march_grid<true, kSlot, kPow2>(shape), shape.block, 0, st>>>(shared, t.ing,
+                                                                                               t.sensors);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long max_ray_blocks, const IngestArgs& shared,
-                                const MarchShape& shape, bool evict, bool slots, cudaStream_t st) {
+                                const MarchShape& shape, bool evict, bool slots, bool pow2, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -935,11 +970,14 @@ cudaError_t launch_batch_update(const BatchTables& t, int max_maps, long long ma
     k_rays_batch<<<(unsigned)rblocks, kRaysBlock, 0, st>>>(t);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     count_launch();
-    if (slots)
-        k_march<true, true><<<march_grid<true, true>(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
-    else
-        k_march<true, false><<<march_grid<true, false>(shape), shape.block, 0, st>>>(shared, t.ing, t.sensors);
-    return cudaGetLastError();
+    if (slots) return pow2 ? launch_march_batch<true, true>(t, shared, shape, st)
+                           : launch_march_batch<true, false>(t, shared, shape, st);
+    return pow2 ? launch_march_batch<false, true>(t, shared, shape, st)
+                : launch_march_batch<false, false>(t, shared, shape, st);
+}
+
+bool pow2_window(const Geom& g) {
+    return ((g.nx & (g.nx - 1)) | (g.ny & (g.ny - 1)) | (g.nz & (g.nz - 1))) == 0;
 }
 
 long long max_segments_per_ray(const Geom& g, int seg_len) {
@@ -994,6 +1032,14 @@ cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d
     return cudaSuccess;
 }
 
+template <bool kSlot, bool kPow2>
+cudaError_t launch_march_one(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
+    const IngestArgs* none = nullptr;
+    const int4* no_sensors = nullptr;
+    return launch_pdl(k_march<false, kSlot, kPow2>, dim3(march_grid<false, kSlot, kPow2>(shape)), dim3(shape.block),
+                      0, st, a, none, no_sensors);
+}
+
 cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     // the work list is empty here: the previous scan's walk emptied it
@@ -1002,13 +1048,10 @@ cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStre
     cudaError_t e = launch_pdl(k_rays, dim3((unsigned)blocks), dim3(kRaysBlock), 0, st, a);
     if (e != cudaSuccess) return e;
     count_launch();
-    const IngestArgs* none = nullptr;
-    const int4* no_sensors = nullptr;
+    const bool pow2 = pow2_window(a.g);
     if (a.slot >= 0)
-        return launch_pdl(k_march<false, true>, dim3(march_grid<false, true>(shape)), dim3(shape.block), 0, st, a,
-                          none, no_sensors);
-    return launch_pdl(k_march<false, false>, dim3(march_grid<false, false>(shape)), dim3(shape.block), 0, st, a, none,
-                      no_sensors);
+        return pow2 ? launch_march_one<true, true>(a, shape, st) : launch_march_one<true, false>(a, shape, st);
+    return pow2 ? launch_march_one<false, true>(a, shape, st) : launch_march_one<false, false>(a, shape, st);
 }
 
 }  // namespace gvom

@@ -393,7 +393,10 @@ class Server:
                         stats.batch_sizes.append(len(batch))
                         progressed = True
             if self.idle_release_s is not None:
-                stats.released_maps += len(door.release_idle(now, self.idle_release_s))
+                released = door.release_idle(now, self.idle_release_s)
+                if released:
+                    stats.released_maps += len(released)
+                    door.retry(now)  # the waiting robots may fit now
             idle = all(s["event"] is None for s in self.slots) and not self.sched.pending()
             if i >= len(reqs) and idle:
                 # everything offered has been served, except scans still
