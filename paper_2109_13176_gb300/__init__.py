@@ -17,7 +17,11 @@ import re
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libgvom.so")
+# GVOM_CHECKED=1 in the environment selects the range-checked debug build
+# (build.build(checked=True)): same ABI, every kernel index checked.
+CHECKED = os.environ.get("GVOM_CHECKED", "0") not in ("", "0")
+LIB_PATH = os.path.join(HERE, "_build", "checked", "libgvom_checked.so") if CHECKED else \
+    os.path.join(HERE, "_build", "libgvom.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 GVOM_OK = 0
@@ -87,7 +91,8 @@ def load_library():
         if _lib is not None:
             return _lib
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"libgvom.so is not built ({LIB_PATH}); run paper_2109_13176_gb300.build.build()")
+            raise RuntimeError(f"the library is not built ({LIB_PATH}); run paper_2109_13176_gb300.build.build("
+                               f"checked={CHECKED})")
         lib = ctypes.CDLL(LIB_PATH)
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         P = ctypes.POINTER
@@ -130,6 +135,9 @@ def load_library():
             "gvom_pipeline_query": ([vp, i64], ctypes.c_int),
             "gvom_pipeline_wait": ([vp, i64], ctypes.c_int),
             "gvom_pipeline_products": ([vp, i64, P(gvom_maps_out)], ctypes.c_int),
+            "gvom_checked_build": ([], ctypes.c_int),
+            "gvom_selftest_wait_timeout": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
+            "gvom_selftest_bounds": ([vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -501,6 +509,24 @@ def gvom_microbench_red(buf, ops: int, seed: int = 1, stream=None) -> None:
 
 def gvom_kernel_launches() -> int:
     return int(load_library().gvom_kernel_launches())
+
+
+def gvom_checked_build() -> bool:
+    """Whether the loaded library is the range-checked build."""
+    return bool(load_library().gvom_checked_build())
+
+
+def gvom_selftest_wait_timeout(handle: int, spin_limit: int = 1000, stream=None) -> None:
+    """Makes a bounded device wait give up (see include/gvom_selftest.h);
+    the next gvom_get_stats reports GVOM_ERR_TIMEOUT."""
+    _check(load_library().gvom_selftest_wait_timeout(handle, int(spin_limit), _stream_handle(stream)),
+           "gvom_selftest_wait_timeout")
+
+
+def gvom_selftest_bounds(handle: int, stream=None) -> None:
+    """Checked builds only: sends an out-of-range index through the range
+    check; the next gvom_get_stats reports GVOM_ERR_BOUNDS."""
+    _check(load_library().gvom_selftest_bounds(handle, _stream_handle(stream)), "gvom_selftest_bounds")
 
 
 # --- convenience --------------------------------------------------------------

@@ -283,6 +283,7 @@ int gvom_get_origin(const gvom_map* m, int64_t out_origin[3]) {
 }
 
 int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:reset");
     if (!m || !origin || !valid_origin(origin)) return GVOM_ERR_INVALID_ARG;
     for (int k = 0; k < 3; ++k) m->origin[k] = origin[k];
     m->buf_head = 0;
@@ -294,6 +295,7 @@ int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
 }
 
 int gvom_shift(gvom_map* m, const int64_t new_origin[3], gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:shift");
     if (!m || !new_origin || !valid_origin(new_origin)) return GVOM_ERR_INVALID_ARG;
     long long d[3];
     bool whole = false, none = true;
@@ -311,6 +313,7 @@ int gvom_shift(gvom_map* m, const int64_t new_origin[3], gvom_stream_t stream) {
 
 int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t stride, const double T_ws[12],
                      gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:ingest");
     if (!m || !T_ws || n < 0 || (stride != 3 && stride != 4)) return GVOM_ERR_INVALID_ARG;
     if (n > 0 && !pts_dev) return GVOM_ERR_INVALID_ARG;
     if (n > GVOM_MAX_SCAN_POINTS) return GVOM_ERR_INVALID_ARG;
@@ -364,6 +367,7 @@ int gvom_update(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, 
 }
 
 int gvom_extract_maps(gvom_map* m, const gvom_maps_out* out, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:extract");
     if (!m || !out) return GVOM_ERR_INVALID_ARG;
     const ExtractParams p = extract_params(m);
     cudaStream_t st = (cudaStream_t)stream;
@@ -377,6 +381,7 @@ int gvom_extract_maps(gvom_map* m, const gvom_maps_out* out, gvom_stream_t strea
 
 int gvom_update_extract(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, int64_t n, int32_t stride,
                         const double T_ws[12], const gvom_maps_out* out, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:update_extract");
     if (!m || !out) return GVOM_ERR_INVALID_ARG;
     const int rc = gvom_update(m, vehicle_xyz, pts_dev, n, stride, T_ws, stream);
     if (rc != GVOM_OK) return rc;
@@ -416,6 +421,7 @@ extern "C" {
 
 int gvom_ingest_multi(gvom_map* m, int32_t k, const float* const* pts_dev, const int64_t* n, int32_t stride,
                       const double* T_ws, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:ingest_multi");
     if (!m || !pts_dev || !n || !T_ws || k < 1 || k > GVOM_MAX_MULTI_SCANS || (stride != 3 && stride != 4))
         return GVOM_ERR_INVALID_ARG;
     if (m->cfg.scan_buffer > 0 && k > m->cfg.scan_buffer) return GVOM_ERR_INVALID_ARG;
@@ -432,6 +438,7 @@ int gvom_ingest_multi(gvom_map* m, int32_t k, const float* const* pts_dev, const
 
 int gvom_export_lut(gvom_map* m, int64_t* lut_dev, uint32_t* data_hits_dev, uint32_t* data_passes_dev,
                     float* data_minz_dev, int64_t data_capacity, int64_t* n_occupied_dev, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:export_lut");
     if (!m || !lut_dev || !n_occupied_dev || data_capacity < 0) return GVOM_ERR_INVALID_ARG;
     if (data_capacity > 0 && (!data_hits_dev || !data_passes_dev || !data_minz_dev)) return GVOM_ERR_INVALID_ARG;
     return cuda_status(gvom::launch_export_lut(m->s, geom_of(m), m->lut_counts, (long long*)n_occupied_dev,
@@ -450,7 +457,8 @@ int gvom_get_stats(gvom_map* m, gvom_stats* out) {
     out->rays_valid = (int64_t)c[gvom::kRaysValid];
     out->hits_in_window = (int64_t)c[gvom::kHitsInWindow];
     out->pass_visits = (int64_t)c[gvom::kPassVisits];
-    return c[gvom::kStatus] != 0 ? GVOM_ERR_TIMEOUT : GVOM_OK;
+    if (c[gvom::kStatus] & gvom::kStatusBounds) return GVOM_ERR_BOUNDS;
+    return (c[gvom::kStatus] & gvom::kStatusTimeout) ? GVOM_ERR_TIMEOUT : GVOM_OK;
 }
 
 int gvom_reset_stats(gvom_map* m, gvom_stream_t stream) {

@@ -227,6 +227,7 @@ int gvom_batch_set_tuning(gvom_batch* b, const gvom_tuning* t) {
 int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, const double* vehicle_xyz,
                     const float* const* pts_dev, const int64_t* n, int32_t stride, const double* T_ws,
                     const gvom_maps_out* outs, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:batch_step");
     if (!b || !maps || !vehicle_xyz || !pts_dev || !n || !T_ws || B < 1 || B > b->max_maps ||
         (stride != 3 && stride != 4))
         return GVOM_ERR_INVALID_ARG;

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kLutBlock) k_lut_count(MapState s, Geom g, lon
         logical_to_phys(g, (uint32_t)i0, k_);
 #pragma unroll
         for (int k = 0; k < kLutPer; ++k)
-            if (i0 + k < V) c += s.hits[k_[k]] != 0u ? 1u : 0u;
+            if (i0 + k < V && in_bounds(k_[k], s.V, s.counters)) c += s.hits[k_[k]] != 0u ? 1u : 0u;
     }
     // the block's total only (a reduction, not a scan)
     c = __reduce_add_sync(0xffffffffu, c);
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kLutBlock)
         h_[k] = 0;
         p_[k] = 0;
         m_[k] = 0.0f;
-        if (i0 + k < V) {
+        if (i0 + k < V && in_bounds(k_[k], s.V, s.counters)) {
             h_[k] = s.hits[k_[k]];
             p_[k] = s.passes[k_[k]];
             m_[k] = s.minz[k_[k]];

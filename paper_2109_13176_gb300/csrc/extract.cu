@@ -16,6 +16,7 @@
 #include <math.h>
 
 #include "gvom_internal.h"
+#include "device_sync.cuh"
 
 namespace gvom {
 
@@ -79,6 +80,7 @@ __device__ __forceinline__ void column_scalar(const MapState& s, const ExtractPa
     int py = cy + g.ry;
     py -= (py >= g.ny) ? g.ny : 0;
     const size_t base = ((size_t)px * g.ny + py) * (size_t)g.nz;
+    if (!in_bounds(base + g.nz - 1, s.V, s.counters)) return;  // the whole warp (one column)
     const uint32_t* __restrict__ hc = s.hits + base;
     const uint32_t* __restrict__ pc = s.passes + base;
     const float* __restrict__ mc = s.minz + base;
@@ -113,7 +115,7 @@ __device__ __forceinline__ void column_scalar(const MapState& s, const ExtractPa
             M += __shfl_xor_sync(0xffffffffu, M, o);
         }
     }
-    if (lane == 0) {
+    if (lane == 0 && in_bounds((size_t)cx * g.ny + cy, (unsigned long long)g.nx * g.ny, s.counters)) {
         const size_t o = (size_t)cx * g.ny + cy;
         if (height) height[o] = any ? h : __int_as_float(0x7fffffff);
         uint8_t f = 0;
@@ -166,6 +168,7 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
         int py = cy + g.ry;
         py -= (py >= g.ny) ? g.ny : 0;
         base = ((size_t)px * g.ny + py) * (size_t)g.nz;
+        if (!in_bounds(base + g.nz - 1, s.V, s.counters)) base = 0;
     }
     const uint4* hc = reinterpret_cast<const uint4*>(s.hits + base);
     const float4* mc = reinterpret_cast<const float4*>(s.minz + base);
@@ -224,7 +227,7 @@ __device__ __forceinline__ void columns_step(const MapState& s, const ExtractPar
             M += __shfl_xor_sync(0xffffffffu, M, o);
         }
     }
-    if (have && sub == 0) {
+    if (have && sub == 0 && in_bounds((size_t)cx * g.ny + cy, (unsigned long long)g.nx * g.ny, s.counters)) {
         const size_t o = (size_t)cx * g.ny + cy;
         if (height) height[o] = col_any ? h : __int_as_float(0x7fffffff);
         uint8_t f = 0;
@@ -271,39 +274,6 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
 constexpr int kTmaCols = 32;      // columns per chunk
 constexpr int kTmaStages = 2;
 constexpr int kTmaBlock = 256;
-constexpr unsigned kSpinLimit = 1u << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// Waits for phase `parity` of the barrier, at most kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (unsigned i = 0; i < kSpinLimit; ++i) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 3 * kTmaCols * nz * sizeof(float); }
 
 // One chunk of kTmaCols consecutive physical columns of one map.
@@ -359,6 +329,10 @@ __device__ __forceinline__ void tma_issue(const ChunkRef& r, int zmax, int stage
     const long long cols = ncols - c0 < kTmaCols ? ncols - c0 : kTmaCols;
     const unsigned bytes = (unsigned)(cols * nz * 4);
     const size_t so = (size_t)stage * kTmaCols * zmax;
+    if (!in_bounds((unsigned long long)(c0 + cols) * nz - 1, r.s.V, r.s.counters)) {
+        mbar_arrive(&bars[stage]);  // nothing copied; the stage completes empty
+        return;
+    }
     mbar_expect_tx(&bars[stage], 3u * bytes);
     bulk_load(hb + so, r.s.hits + c0 * nz, bytes, &bars[stage]);
     bulk_load(mb + so, r.s.minz + c0 * nz, bytes, &bars[stage]);
@@ -457,7 +431,7 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
                 M += __shfl_xor_sync(0xffffffffu, M, o);
             }
         }
-        if (have && sub == 0) {
+        if (have && sub == 0 && in_bounds((unsigned long long)pc * nz + nz - 1, r.s.V, r.s.counters)) {
             // window coordinates of the physical column
             const int px = (int)((unsigned)pc / (unsigned)g.ny), py = (int)((unsigned)pc % (unsigned)g.ny);
             int cx = px - g.rx;
@@ -489,7 +463,7 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
             if (c >= nchunks) break;
             mbar_wait(&bars[q % kTmaStages], (unsigned)((q / kTmaStages) & 1));
         }
-        atomicOr(src.at(blockIdx.x + (long long)k * gridDim.x).s.counters + kStatus, 1ull);
+        atomicOr(src.at(blockIdx.x + (long long)k * gridDim.x).s.counters + kStatus, kStatusTimeout);
     }
 }
 
@@ -815,6 +789,7 @@ __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits,
         int pz = cz + g.rz;
         pz -= (pz >= g.nz) ? g.nz : 0;
         const size_t k = ((size_t)px * g.ny + py) * (size_t)g.nz + pz;
+        if (!in_bounds(k, s.V, s.counters)) continue;
         if (hits) hits[i] = s.hits[k];
         if (passes) passes[i] = s.passes[k];
         if (minz) minz[i] = s.minz[k];

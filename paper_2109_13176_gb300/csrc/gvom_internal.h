@@ -6,9 +6,21 @@
 
 #include <atomic>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gvom.h"
 
 namespace gvom {
+
+// An NVTX range around one phase of a call (visible in Nsight tools as
+// gvom:<phase> on the calling thread; no cost worth measuring without a tool
+// attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Programmatic dependent launch. The path's kernels are launched with
 // launch_pdl: a kernel waits until its predecessor's memory is visible
@@ -62,9 +74,32 @@ struct MapState {
     uint32_t V;                    // voxels of the window (< 2^31)
 };
 
-// counters[kStatus] != 0: a bounded device wait of one of the map's kernels
-// gave up (reported by gvom_get_stats as GVOM_ERR_TIMEOUT).
+// counters[kStatus]: bit kStatusTimeout -- a bounded device wait of one of
+// the map's kernels gave up (gvom_get_stats: GVOM_ERR_TIMEOUT); bit
+// kStatusBounds -- a checked build caught an index out of range
+// (GVOM_ERR_BOUNDS).
 enum Counter { kPointsIn = 0, kRaysValid = 1, kHitsInWindow = 2, kPassVisits = 3, kStatus = 4, kCounters = 5 };
+constexpr unsigned long long kStatusTimeout = 1ull;
+constexpr unsigned long long kStatusBounds = 2ull;
+
+#ifdef __CUDACC__
+// Range check of a computed index. In a checked build (GVOM_CHECKED), an
+// index at or past n records kStatusBounds in the status word (when there
+// is one) and the caller skips the access; otherwise it is always true and
+// costs nothing.
+__device__ __forceinline__ bool in_bounds(unsigned long long i, unsigned long long n, unsigned long long* counters) {
+#ifdef GVOM_CHECKED
+    if (i < n) return true;
+    if (counters) atomicOr(counters + kStatus, kStatusBounds);
+    return false;
+#else
+    (void)i;
+    (void)n;
+    (void)counters;
+    return true;
+#endif
+}
+#endif
 
 // Per-scan scratch of the two-phase ingest, owned by the map: one record
 // per point (quantised endpoint and its number of traversal segments), the

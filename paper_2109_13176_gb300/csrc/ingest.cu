@@ -208,19 +208,24 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
         const int ex = q[0] >> 8, ey = q[1] >> 8, ez = q[2] >> 8;
         if (in_window(g, ex, ey, ez)) {
             const uint32_t k = phys_index(g, ex, ey, ez);
-            atomicAdd(a.s.hits + k, 1u);
-            atomic_min_f32(a.s.minz + k, wz);
+            if (in_bounds(k, a.s.V, a.s.counters)) {
+                atomicAdd(a.s.hits + k, 1u);
+                atomic_min_f32(a.s.minz + k, wz);
+            }
             if (a.slot >= 0) {
                 const size_t o = (size_t)a.slot * a.s.V + k;
-                atomicAdd(a.s.ring_hits + o, 1u);
-                atomic_min_f32(a.s.ring_minz + o, wz);
+                if (in_bounds(o, (unsigned long long)a.s.ring_K * a.s.V, a.s.counters)) {
+                    atomicAdd(a.s.ring_hits + o, 1u);
+                    atomic_min_f32(a.s.ring_minz + o, wz);
+                }
             }
             hit_in_window = 1;
         }
         RayFrame f;
         if (ray_frame(g, qo, q, f)) nseg = (f.khi - f.klo) / a.seg_len + 1;
     }
-    if (i < a.n) a.w.rays[ray_base + i] = make_int4(q[0], q[1], q[2], (int)((map_id << 16) | (unsigned)nseg));
+    if (i < a.n && in_bounds(ray_base + i, a.w.cap_points, a.s.counters))
+        a.w.rays[ray_base + i] = make_int4(q[0], q[1], q[2], (int)((map_id << 16) | (unsigned)nseg));
 
     // Reserve this block's slots in the work list with one atomic, then lay
     // each warp's segments out segment-major (all first segments of the
@@ -517,9 +522,11 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
         unsigned int own_item = own;  // entry owning the counters of this lane's item's map
         uint32_t* passes = a1.s.passes;
         uint32_t* spasses = nullptr;
+        uint32_t vmap = a1.s.V;  // voxels of this lane's map (range checks)
+        unsigned long long* cnts = a1.s.counters;
         if (kSlot && !kBatch) spasses = a1.s.ring_passes + (size_t)a1.slot * a1.s.V;
         unsigned long long item_visits = 0;
-        if (idx < n_items) {
+        if (idx < n_items && in_bounds(a1.w.items[idx].x, a1.w.cap_points, a1.s.counters)) {
             const uint2 it = a1.w.items[idx];
             const int4 r = a1.w.rays[it.x];
             const int b[3] = {r.x, r.y, r.z};
@@ -528,6 +535,8 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 const int4 sq = sensors[map];
                 const int qo[3] = {sq.x, sq.y, sq.z};
                 passes = descs[map].s.passes;
+                vmap = descs[map].s.V;
+                cnts = descs[map].s.counters;
                 own_item = (unsigned int)descs[map].cnt_owner;
                 if (kSlot) {
                     const int sl = descs[map].slot;
@@ -561,7 +570,7 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 boundary = lane == 0 || prev != key;
             }
             const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-            if (inside && boundary) {
+            if (inside && boundary && in_bounds(key, vmap, cnts)) {
                 const unsigned int after = starts & ~((2u << lane) - 1u);
                 const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
                 atomicAdd(passes + key, run);
@@ -615,6 +624,7 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
 // combined state, and where an emptied slot held the combined lowest
 // return, that becomes the minimum over the slots that stay (+inf if none).
 __device__ __forceinline__ void evict_voxel(const MapState& s, unsigned long long mask, uint32_t i) {
+    if (!in_bounds(i, s.V, s.counters)) return;
     uint32_t h = 0u, p = 0u;
     bool gone = false;
     for (int j = 0; j < s.ring_K; ++j) {
@@ -648,6 +658,7 @@ __device__ __forceinline__ void evict_voxel(const MapState& s, unsigned long lon
 // load per array and slot finds the common case, four voxels that no
 // emptied slot touched.
 __device__ __forceinline__ void evict_quad(const MapState& s, unsigned long long mask, uint32_t i) {
+    if (!in_bounds(i + 3ull, s.V, s.counters)) return;
     if ((mask & (mask - 1ull)) == 0ull) {
         // one slot (every scan of the plain and batched paths): the counts of
         // the four voxels leave the map with 16-byte loads and stores
@@ -732,6 +743,7 @@ __device__ __forceinline__ uint32_t column_base(const Geom& g, int cx, int cy) {
 }
 
 __device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
+    if (!in_bounds(k, s.V, s.counters)) return;
     s.hits[k] = 0u;
     s.passes[k] = 0u;
     s.minz[k] = __int_as_float(0x7f800000);

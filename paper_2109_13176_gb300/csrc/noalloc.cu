@@ -60,6 +60,7 @@ bool aligned(const void* p, uintptr_t a) { return (((uintptr_t)p) & (a - 1)) == 
 
 extern "C" int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t* hits_dev, const uint32_t* passes_dev,
                                          const float* minz_dev, const gvom_maps_out* out, gvom_stream_t stream) {
+    gvom::NvtxRange nvtx_range("gvom:extract_noalloc");
     if (!gvom::valid_config(cfg) || !hits_dev || !passes_dev || !minz_dev || !out) return GVOM_ERR_INVALID_ARG;
     if ((long long)cfg->nx * cfg->ny > kNoallocMaxPixels) return GVOM_ERR_INVALID_ARG;
     // The column pass reads a grid whose nz is a multiple of 4 with 16-byte

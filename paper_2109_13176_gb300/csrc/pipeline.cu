@@ -102,6 +102,7 @@ int gvom_pipeline_create(gvom_map* map, int64_t max_points, gvom_pipeline** out)
 
 int gvom_pipeline_submit(gvom_pipeline* p, const double vehicle_xyz[3], const float* pts_host, int64_t n,
                          int32_t stride, const double T_ws[12], const gvom_maps_out* out_host, int64_t* ticket) {
+    gvom::NvtxRange nvtx_range("gvom:pipeline_submit");
     if (!p || !vehicle_xyz || !T_ws || !ticket || n < 0 || n > p->max_points || (stride != 3 && stride != 4) ||
         (n > 0 && !pts_host))
         return GVOM_ERR_INVALID_ARG;

@@ -1,0 +1,147 @@
+"""Failure detection on the GPU without a fault (the paper has none of it):
+
+- a bounded device wait that nothing completes gives up after its
+  iteration limit, gvom_get_stats reports GVOM_ERR_TIMEOUT, and after
+  gvom_reset_stats the same map updates exactly like the oracle again;
+- the range-checked build (GVOM_CHECKED) runs the path on small maps with
+  no violation and results equal to the oracle's, and an index one past the
+  map sent through its range check is reported as GVOM_ERR_BOUNDS with the
+  access skipped.
+"""
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_13176_gb300 import build
+    build.build()
+    import paper_2109_13176_gb300 as m
+    return m
+
+
+def stats_status(gv, m):
+    st = gv.gvom_stats()
+    return gv.load_library().gvom_get_stats(m.handle, ctypes.byref(st))
+
+
+def test_bounded_wait_gives_up_and_the_map_stays_usable(gv):
+    s = synth.single_scan()
+    ms = synth.WORKLOADS["single_scan"]["map"]
+    m = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res)
+    assert gv.load_library().gvom_selftest_wait_timeout(m.handle, 0, None) == gv.GVOM_ERR_INVALID_ARG
+    gv.gvom_selftest_wait_timeout(m.handle, 2000)
+    torch.cuda.synchronize()
+    assert stats_status(gv, m) == gv.GVOM_ERR_TIMEOUT
+    m.reset_stats()
+    assert stats_status(gv, m) == gv.GVOM_OK
+    # the context and the map work as before
+    om = oracle.OracleMap(oracle.OracleParams(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res))
+    om.shift_for_pose(s.vehicle_xyz)
+    om.ingest(s.points, s.T_ws)
+    m.update(s.vehicle_xyz, torch.from_numpy(s.points).cuda(), s.T_ws)
+    hits, passes, minz = (t.cpu().numpy() for t in m.extract_voxels())
+    np.testing.assert_array_equal(hits.view(np.uint32), om.hits)
+    np.testing.assert_array_equal(passes.view(np.uint32), om.passes)
+    assert stats_status(gv, m) == gv.GVOM_OK
+    m.close()
+
+
+def test_unchecked_build_refuses_the_bounds_selftest(gv):
+    if gv.gvom_checked_build():
+        pytest.skip("this process loaded the checked build")
+    m = gv.VoxelMap(nx=16, ny=16, nz=8, res=0.2)
+    assert gv.load_library().gvom_selftest_bounds(m.handle, None) == gv.GVOM_ERR_INVALID_ARG
+    assert stats_status(gv, m) == gv.GVOM_OK
+    m.close()
+
+
+_CHECKED_RUN = r"""
+import ctypes, math, sys
+import numpy as np, torch
+import oracle, synth
+from paper_2109_13176_gb300 import build
+build.build(checked=True)
+import paper_2109_13176_gb300 as gv
+assert gv.gvom_checked_build()
+lib = gv.load_library()
+
+def status(m):
+    st = gv.gvom_stats()
+    return lib.gvom_get_stats(m.handle, ctypes.byref(st))
+
+def same_as_oracle(m, om):
+    h, p, z = (t.cpu().numpy() for t in m.extract_voxels())
+    assert np.array_equal(h.view(np.uint32), om.hits) and np.array_equal(p.view(np.uint32), om.passes)
+    assert np.array_equal(z, om.minz)
+    out = {k: v.cpu().numpy() for k, v in m.extract_maps().items()}
+    ref = om.extract()
+    assert np.array_equal(out["flags"], ref["flags"]) and np.array_equal(out["height"], ref["height"], equal_nan=True)
+
+scan = synth.single_scan()
+cfg, seq = synth.sequence_scans("sequence", n_scans=2, stride=4)
+checked = 0
+# a power-of-two window and an odd-sized one (both walk variants, all column passes)
+for dims, buf in (((128, 128, 32), 0), ((100, 90, 30), 0), ((96, 96, 32), 2)):
+    p = oracle.OracleParams(nx=dims[0], ny=dims[1], nz=dims[2], res=0.2)
+    om = oracle.BufferedOracleMap(p, 2) if buf else oracle.OracleMap(p)
+    m = gv.VoxelMap(nx=dims[0], ny=dims[1], nz=dims[2], res=0.2, scan_buffer=buf)
+    for s in [scan] + seq:
+        om.shift_for_pose(s.vehicle_xyz)
+        om.ingest(s.points, s.T_ws)
+        m.update(s.vehicle_xyz, torch.from_numpy(s.points).cuda(), s.T_ws)
+        same_as_oracle(m, om)
+    V = dims[0] * dims[1] * dims[2]
+    lut = torch.empty(V, dtype=torch.int64, device="cuda")
+    d = [torch.empty(V, dtype=t, device="cuda") for t in (torch.int32, torch.int32, torch.float32)]
+    n_occ = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gv.gvom_export_lut(m.handle, lut, d[0], d[1], d[2], V, n_occ)
+    torch.cuda.synchronize()
+    assert status(m) == gv.GVOM_OK, status(m)
+    checked += 1
+    m.close()
+# a batch step of three maps
+maps = [gv.VoxelMap(nx=64, ny=64, nz=32, res=0.2) for _ in range(3)]
+batch = gv.MapBatch(3, 3 * len(scan.points), graph=True)
+pts = [torch.from_numpy(scan.points).cuda()] * 3
+outs = [mm.alloc_maps() for mm in maps]
+batch.step(maps, [scan.vehicle_xyz] * 3, pts, [scan.T_ws] * 3, outs=outs)
+torch.cuda.synchronize()
+assert all(status(mm) == gv.GVOM_OK for mm in maps)
+# the range check itself: one past the last voxel is caught, nothing is written
+mm = maps[0]
+before = [t.clone() for t in mm.extract_voxels()]
+gv.gvom_selftest_bounds(mm.handle)
+torch.cuda.synchronize()
+assert status(mm) == gv.GVOM_ERR_BOUNDS
+assert all(torch.equal(a, b) for a, b in zip(before, mm.extract_voxels()))
+mm.reset_stats()
+assert status(mm) == gv.GVOM_OK
+batch.close()
+for mm in maps:
+    mm.close()
+print("CHECKED_OK", checked)
+"""
+
+
+def test_checked_build_runs_clean_and_catches_an_out_of_range_index(gv):
+    env = dict(os.environ, GVOM_CHECKED="1")
+    r = subprocess.run([sys.executable, "-c", _CHECKED_RUN], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=1200)
+    assert r.returncode == 0, (r.stdout[-2000:], r.stderr[-3000:])
+    assert "CHECKED_OK 3" in r.stdout
