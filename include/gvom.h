@@ -254,6 +254,18 @@ GVOM_API int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t* h
 GVOM_API int gvom_extract_voxels(struct gvom_map* map, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
                         gvom_stream_t stream);
 
+/* Checkpoint restore (the paper has no counterpart; for restarting a
+ * server or moving a map between processes). Replaces the whole state of a
+ * map without a scan buffer: the window is placed at `origin` and its
+ * voxels take the caller's arrays, in logical (window) order as
+ * gvom_extract_voxels writes them (nx*ny*nz elements each, 4-byte
+ * aligned). A checkpoint is gvom_get_origin plus gvom_extract_voxels; the
+ * counters of gvom_get_stats are not part of it. Maps with a scan buffer
+ * (scan_buffer > 0) cannot be restored this way, because their per-scan
+ * slots are not exported: GVOM_ERR_INVALID_ARG. Stream-ordered. */
+GVOM_API int gvom_import_state(struct gvom_map* map, const int64_t origin[3], const uint32_t* hits_dev,
+                               const uint32_t* passes_dev, const float* minz_dev, gvom_stream_t stream);
+
 /* Folds k scans from different sensors into the map in one per-point pass
  * and one traversal launch (Sec. III: several pointclouds feed one map).
  * Scan j has n[j] points at pts_dev[j] (device, same stride for all, as

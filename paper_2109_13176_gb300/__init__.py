@@ -136,6 +136,7 @@ def load_library():
             "gvom_pipeline_wait": ([vp, i64], ctypes.c_int),
             "gvom_pipeline_products": ([vp, i64, P(gvom_maps_out)], ctypes.c_int),
             "gvom_checked_build": ([], ctypes.c_int),
+            "gvom_import_state": ([vp, o3, vp, vp, vp, vp], ctypes.c_int),
             "gvom_selftest_wait_timeout": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
             "gvom_selftest_bounds": ([vp, vp], ctypes.c_int),
         }
@@ -336,6 +337,13 @@ def gvom_export_lut(handle: int, lut, data_hits, data_passes, data_minz, data_ca
 def gvom_extract_voxels(handle: int, hits=None, passes=None, minz=None, stream=None) -> None:
     ptrs = [t.data_ptr() if t is not None else None for t in (hits, passes, minz)]
     _check(load_library().gvom_extract_voxels(handle, *ptrs, _stream_handle(stream)), "gvom_extract_voxels")
+
+
+def gvom_import_state(handle: int, origin, hits, passes, minz, stream=None) -> None:
+    """Restores a checkpoint (origin + logical voxel arrays) into a map
+    without a scan buffer (see include/gvom.h)."""
+    _check(load_library().gvom_import_state(handle, _i64(origin), hits.data_ptr(), passes.data_ptr(), minz.data_ptr(),
+                                            _stream_handle(stream)), "gvom_import_state")
 
 
 def gvom_get_stats(handle: int) -> dict:
@@ -637,6 +645,15 @@ class VoxelMap:
     def update_extract(self, vehicle_xyz, points, T_ws, out, stream=None):
         gvom_update_extract(self.handle, vehicle_xyz, points, T_ws, out, stream)
         return out
+
+    def checkpoint(self, stream=None):
+        """(origin, hits, passes, minz): the map's window and its voxels in
+        logical order (device tensors); gvom_import_state restores it."""
+        return (tuple(self.origin),) + tuple(self.extract_voxels(stream))
+
+    def restore(self, checkpoint, stream=None):
+        origin, hits, passes, minz = checkpoint
+        gvom_import_state(self.handle, origin, hits, passes, minz, stream)
 
     def ingest_multi(self, points, T_ws, stream=None):
         gvom_ingest_multi(self.handle, points, T_ws, stream)

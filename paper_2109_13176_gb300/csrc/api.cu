@@ -388,6 +388,17 @@ int gvom_update_extract(gvom_map* m, const double vehicle_xyz[3], const float* p
     return gvom_extract_maps(m, out, stream);
 }
 
+int gvom_import_state(gvom_map* m, const int64_t origin[3], const uint32_t* hits_dev, const uint32_t* passes_dev,
+                      const float* minz_dev, gvom_stream_t stream) {
+    if (!m || !origin || !valid_origin(origin) || !hits_dev || !passes_dev || !minz_dev) return GVOM_ERR_INVALID_ARG;
+    if (m->cfg.scan_buffer != 0) return GVOM_ERR_INVALID_ARG;  // a buffer's per-scan slots cannot be restored
+    if ((((uintptr_t)hits_dev) | ((uintptr_t)passes_dev) | ((uintptr_t)minz_dev)) & 3u) return GVOM_ERR_INVALID_ARG;
+    gvom::NvtxRange nvtx_range("gvom:import_state");
+    for (int k = 0; k < 3; ++k) m->origin[k] = origin[k];
+    return cuda_status(gvom::launch_scatter_voxels(m->s, geom_of(m), hits_dev, passes_dev, minz_dev,
+                                                   (cudaStream_t)stream));
+}
+
 int gvom_extract_voxels(gvom_map* m, uint32_t* hits_dev, uint32_t* passes_dev, float* minz_dev,
                         gvom_stream_t stream) {
     if (!m) return GVOM_ERR_INVALID_ARG;

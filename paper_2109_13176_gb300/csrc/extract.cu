@@ -796,6 +796,30 @@ __global__ void k_gather_voxels(MapState s, Geom g, uint32_t* __restrict__ hits,
     }
 }
 
+// The inverse of k_gather_voxels: logical (window-order) arrays into the
+// toroidal state.
+__global__ void k_scatter_voxels(MapState s, Geom g, const uint32_t* __restrict__ hits,
+                                 const uint32_t* __restrict__ passes, const float* __restrict__ minz) {
+    const long long V = (long long)g.nx * g.ny * g.nz;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V; i += stride) {
+        const int cz = (int)(i % g.nz);
+        const long long col = i / g.nz;
+        const int cy = (int)(col % g.ny), cx = (int)(col / g.ny);
+        int px = cx + g.rx;
+        px -= (px >= g.nx) ? g.nx : 0;
+        int py = cy + g.ry;
+        py -= (py >= g.ny) ? g.ny : 0;
+        int pz = cz + g.rz;
+        pz -= (pz >= g.nz) ? g.nz : 0;
+        const size_t k = ((size_t)px * g.ny + py) * (size_t)g.nz + pz;
+        if (!in_bounds(k, s.V, s.counters)) continue;
+        s.hits[k] = hits[i];
+        s.passes[k] = passes[i];
+        s.minz[k] = minz[i];
+    }
+}
+
 int sm_count() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -910,6 +934,17 @@ cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, f
     dim3 grid((p.g.ny + tile - 1) / tile, (p.g.nx + tile - 1) / tile);
     count_launch();
     return launch_pdl(k_slope_negative, grid, dim3(kPxBlock), smem, st, p, height, slope, rough, flags);
+}
+
+cudaError_t launch_scatter_voxels(const MapState& s, const Geom& g, const uint32_t* hits, const uint32_t* passes,
+                                  const float* minz, cudaStream_t st) {
+    const long long V = (long long)g.nx * g.ny * g.nz;
+    long long blocks = (V + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    count_launch();
+    k_scatter_voxels<<<(unsigned)blocks, 256, 0, st>>>(s, g, hits, passes, minz);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,

@@ -247,6 +247,8 @@ cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, f
                                   uint8_t* flags, cudaStream_t st);
 cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,
                                  cudaStream_t st);
+cudaError_t launch_scatter_voxels(const MapState& s, const Geom& g, const uint32_t* hits, const uint32_t* passes,
+                                  const float* minz, cudaStream_t st);
 
 __host__ __device__ inline long long floor_mod(long long a, long long n) {
     long long r = a % n;

@@ -337,6 +337,7 @@ struct Walk {
     int nA, nB;         // window extents of the minor axes
     int exitA, exitB;   // the first minor voxel past the window in the walk's direction
     int sM, sA, sB;     // 256 den per axis
+    int nsM, nsA;       // -sM, -sA
     int dMA, dMB, dAB;  // pairwise crossing-time differences
     int tMA, tAM, tMB, tBM, tAB, tBA;  // tie thresholds: i first iff D_ij < t_ij
     int total;          // crossings left to the endpoint
@@ -356,6 +357,21 @@ struct Walk {
 };
 
 __device__ __forceinline__ int rank_of(int dir) { return dir > 0 ? 0 : 1; }
+
+// a * b + c as an integer multiply-add. The walk's step is bound by the
+// integer ALU pipe while the FMA pipe (which executes integer multiply-adds)
+// idles, so the step's conditional updates are written as products with the
+// 0/1 step flags.
+__device__ __forceinline__ int imad_s32(int a, int b, int c) {
+    int d;
+    asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t imad_u32(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
 
 // Builds the walk of segment j of the ray to endpoint b. False if the ray
 // has no voxel to count in the window.
@@ -414,6 +430,8 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     w.sM = (int)(256 * den[0]);
     w.sA = (int)(256 * den[1]);
     w.sB = (int)(256 * den[2]);
+    w.nsM = -w.sM;
+    w.nsA = -w.sA;
     w.dMA = (int)(num[0] * den[1] - num[1] * den[0]);
     w.dMB = (int)(num[0] * den[2] - num[2] * den[0]);
     w.dAB = (int)(num[1] * den[2] - num[2] * den[1]);
@@ -582,19 +600,21 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
             const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
             // the major step past the segment's last slab ends the segment
             live = live && !(gM && w.segM == 0);
-            w.segM -= gM ? 1 : 0;
+            const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
+            w.segM = imad_s32(iM, -1, w.segM);
             if (kPow2) {
-                w.key = ((w.key + (gM ? w.stM : 0u)) & w.fmM) | ((w.key + (gA ? w.stA : 0u)) & w.fmA) |
-                        ((w.key + (gB ? w.stB : 0u)) & w.fmB);
+                w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
+                        ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
+                        ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
             } else {
-                w.cM += gM ? w.dirM : 0;
+                w.cM = imad_s32(iM, w.dirM, w.cM);
             }
-            w.cA += gA ? w.dirA : 0;
-            w.cB += gB ? w.dirB : 0;
-            w.dMA += (gM ? w.sA : 0) - (gA ? w.sM : 0);
-            w.dMB += (gM ? w.sB : 0) - (gB ? w.sM : 0);
-            w.dAB += (gA ? w.sB : 0) - (gB ? w.sA : 0);
-            w.total -= (int)gM + (int)gA + (int)gB;
+            w.cA = imad_s32(iA, w.dirA, w.cA);
+            w.cB = imad_s32(iB, w.dirB, w.cB);
+            w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
+            w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
+            w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
+            w.total = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.total)));
             // a minor axis past the window never comes back (steps are unit,
             // so it passes the window exactly at its exit voxel)
             live = live && w.cA != w.exitA && w.cB != w.exitB;

@@ -145,3 +145,34 @@ def test_checked_build_runs_clean_and_catches_an_out_of_range_index(gv):
                        timeout=1200)
     assert r.returncode == 0, (r.stdout[-2000:], r.stderr[-3000:])
     assert "CHECKED_OK 3" in r.stdout
+
+
+def test_checkpoint_restore_continues_like_the_original(gv):
+    # a map checkpointed after two scans and restored into a fresh map
+    # (another window origin first) continues bit for bit like the original
+    cfg, scans = synth.sequence_scans("sequence", n_scans=4, stride=3)
+    ms = cfg.map
+    kw = dict(nx=96, ny=80, nz=32, res=ms.res)
+    a = gv.VoxelMap(**kw)
+    for s in scans[:2]:
+        a.update(s.vehicle_xyz, torch.from_numpy(s.points).cuda(), s.T_ws)
+    ck = a.checkpoint()
+    b = gv.VoxelMap(**kw)
+    b.shift((7, -3, 2))
+    b.restore(ck)
+    assert tuple(b.origin) == tuple(a.origin)
+    for s in scans[2:]:
+        for m in (a, b):
+            m.update(s.vehicle_xyz, torch.from_numpy(s.points).cuda(), s.T_ws)
+    for x, y in zip(a.extract_voxels(), b.extract_voxels()):
+        assert torch.equal(x, y)
+    oa, ob = a.extract_maps(), b.extract_maps()
+    for k in oa:
+        np.testing.assert_array_equal(oa[k].cpu().numpy(), ob[k].cpu().numpy())
+    # a map with a scan buffer cannot be restored from a plain checkpoint
+    c = gv.VoxelMap(scan_buffer=2, **kw)
+    o = (ctypes.c_int64 * 3)(*ck[0])
+    assert gv.load_library().gvom_import_state(c.handle, o, ck[1].data_ptr(), ck[2].data_ptr(), ck[3].data_ptr(),
+                                               None) == gv.GVOM_ERR_INVALID_ARG
+    for m in (a, b, c):
+        m.close()
