@@ -331,19 +331,57 @@ __device__ __forceinline__ long long floor_div_small(long long x, long long y) {
     return q;
 }
 
+// The crossing of an axis at t = num / den (its ordering rank: 0 for an
+// upward crossing, which takes effect at t, 1 for a downward one, which
+// takes effect just after t). Within one ray num <= |d| + 256 < 2^24 and
+// den = |d| < 2^23 (1/256-voxel units), so both fit 32 bits and their
+// products 64.
+struct Crossing {
+    int num, den;
+    int rank;
+};
+
+// Whether crossing x comes before crossing y in the walk's order (t, then
+// upward before downward). Exact.
+__device__ __forceinline__ bool cross_before(const Crossing& x, const Crossing& y) {
+    const long long l = (long long)x.num * y.den, r = (long long)y.num * x.den;
+    return l < r || (l == r && x.rank < y.rank);
+}
+
+// How many of an axis's crossings -- the next one at num / den, then one
+// every 256 / den, `tot` in all, rank rk -- come no later than crossing e
+// in the walk's order (the crossings sharing e's time and rank included).
+__device__ __forceinline__ int crossings_upto(int num, int den, int tot, int rk, const Crossing& e) {
+    if (tot <= 0) return 0;
+    // crossing k (k = 0, 1, ...) comes no later than e iff 256 k den_e <= X,
+    // strictly below X when it would step after e at an equal time
+    const long long X = (long long)e.num * den - (long long)num * e.den;
+    const long long Y = 256LL * e.den;
+    long long c;
+    if (rk <= e.rank)
+        c = X < 0 ? 0 : floor_div_small(X, Y) + 1;
+    else
+        c = X <= 0 ? 0 : floor_div_small(X - 1, Y) + 1;
+    return (int)(c < (long long)tot ? c : (long long)tot);
+}
+
+// The walk of one segment, from its first voxel in the window. rem counts
+// the crossings still to take: the walk visits its current voxel, takes the
+// next crossing group and stops when rem reaches zero, which happens exactly
+// on the group that leaves the segment's last major slab, leaves the window
+// along a minor axis, or enters the ray's endpoint voxel (whichever comes
+// first). Every voxel it visits is therefore in the window and not the
+// endpoint voxel: the loop needs no window, exit or endpoint test.
 struct Walk {
-    int cM, cA, cB;     // current voxel, window coordinates
+    int cM, cA, cB;     // current voxel, window coordinates (the index of non-power-of-two windows)
     int dirM, dirA, dirB;
-    int nA, nB;         // window extents of the minor axes
-    int exitA, exitB;   // the first minor voxel past the window in the walk's direction
+    int nM, nA, nB;     // window extents
     int sM, sA, sB;     // 256 den per axis
     int nsM, nsA;       // -sM, -sA
     int dMA, dMB, dAB;  // pairwise crossing-time differences
     int tMA, tAM, tMB, tBM, tAB, tBA;  // tie thresholds: i first iff D_ij < t_ij
-    int total;          // crossings left to the endpoint
-    int segM;           // major steps left in this segment
+    int rem;            // crossings left to take
     int rM, rA, rB;     // ring offsets
-    int nM;
     uint32_t kM, kA, kB;  // strides of the state array per role
     // Windows whose extents are all powers of two: the physical index of the
     // current voxel is kept up to date instead of being recomputed. Axis k
@@ -373,8 +411,8 @@ __device__ __forceinline__ uint32_t imad_u32(uint32_t a, uint32_t b, uint32_t c)
     return d;
 }
 
-// Builds the walk of segment j of the ray to endpoint b. False if the ray
-// has no voxel to count in the window.
+// Builds the walk of segment j of the ray to endpoint b. False if the
+// segment has no voxel to count in the window.
 __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], const int b[3], int j, Walk& w) {
     const Geom& g = a.g;
     RayFrame f;
@@ -382,7 +420,7 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     const int M = f.M, A = M == 0 ? 1 : 0, B = M == 2 ? 1 : 2;
     const int kstart = f.klo + j * a.seg_len;
     const int kend = min(f.khi, kstart + a.seg_len - 1);
-    w.segM = kend - kstart;
+    const int segM = kend - kstart;  // major steps from the first slab to the last
 
     const int aM = sel3(f.a, M), dM = sel3(f.d, M);
     const int dirM = dM > 0 ? 1 : -1;
@@ -391,9 +429,10 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     const long long numFirst = dirM > 0 ? 256LL * (c0M + 1) - aM : (long long)aM - 256LL * c0M;
     const long long numStar = numFirst + 256LL * (kstart - 1);
 
-    int c[3], dir[3];
-    long long num[3], den[3];
-    int total = 0;
+    // the segment's first voxel, and per role its next crossing (num / den),
+    // direction, rank and the number of crossings left to the endpoint
+    int c[3], dir[3], tot[3], rk[3];
+    int num[3], den[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         const int k = r == 0 ? M : (r == 1 ? A : B);
@@ -413,46 +452,105 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
         if (dk != 0) {
             dir[r] = dk > 0 ? 1 : -1;
             den[r] = dk > 0 ? dk : -dk;
-            num[r] = dk > 0 ? 256LL * (ck + 1) - ak : (long long)ak - 256LL * ck;
-            total += dk > 0 ? ce - ck : ck - ce;
+            num[r] = dk > 0 ? 256 * (ck + 1) - ak : ak - 256 * ck;
+            tot[r] = dk > 0 ? ce - ck : ck - ce;
         } else {
             dir[r] = 1;
             den[r] = 1;
             num[r] = 2;
+            tot[r] = 0;
+        }
+        rk[r] = rank_of(dir[r]);
+    }
+    const int n3[3] = {dim_of(g, M), dim_of(g, A), dim_of(g, B)};
+    // a minor axis already past the window has nothing left to count
+    if ((dir[1] > 0 ? c[1] >= n3[1] : c[1] < 0) || (dir[2] > 0 ? c[2] >= n3[2] : c[2] < 0)) return false;
+
+    // The end E: the earliest of the crossing out of the segment's last
+    // major slab, the crossing out of the window along A or B, and the ray's
+    // last crossing (into the endpoint voxel).
+    Crossing E = {0, 1, 0}, last = {0, 1, 0};
+    bool have_e = false, have_last = false;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        if (tot[r] > 0) {
+            const Crossing x = {num[r] + 256 * (tot[r] - 1), den[r], rk[r]};
+            if (!have_last || cross_before(last, x)) last = x;
+            have_last = true;
+        }
+    if (!have_last) return false;  // the segment starts in the endpoint voxel
+    E = last;
+    have_e = true;
+    if (segM + 1 <= tot[0]) {
+        const Crossing x = {num[0] + 256 * segM, den[0], rk[0]};
+        if (cross_before(x, E)) E = x;
+    }
+#pragma unroll
+    for (int r = 1; r < 3; ++r) {
+        const int exit_v = dir[r] > 0 ? n3[r] : -1;
+        const int n = dir[r] > 0 ? exit_v - c[r] : c[r] - exit_v;
+        if (n >= 1 && n <= tot[r]) {
+            const Crossing x = {num[r] + 256 * (n - 1), den[r], rk[r]};
+            if (cross_before(x, E)) E = x;
         }
     }
+    (void)have_e;
+
+    // The start S: when the segment begins before the window along A or B,
+    // the later of the crossings into it.
+    Crossing S = {0, 1, 0};
+    bool have_s = false;
+#pragma unroll
+    for (int r = 1; r < 3; ++r) {
+        const bool before = dir[r] > 0 ? c[r] < 0 : c[r] >= n3[r];
+        if (!before) continue;
+        const int n = dir[r] > 0 ? -c[r] : c[r] - (n3[r] - 1);
+        if (n > tot[r]) return false;  // the ray ends before it enters
+        const Crossing x = {num[r] + 256 * (n - 1), den[r], rk[r]};
+        if (!have_s || cross_before(S, x)) S = x;
+        have_s = true;
+    }
+    int rem = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int ce_r = crossings_upto(num[r], den[r], tot[r], rk[r], E);
+        int cs_r = 0;
+        if (have_s) {
+            cs_r = crossings_upto(num[r], den[r], tot[r], rk[r], S);
+            // move past S's group: its voxel is the first in the window
+            c[r] += dir[r] * cs_r;
+            num[r] += 256 * cs_r;
+        }
+        rem += ce_r - cs_r;
+    }
+    if (rem <= 0) return false;  // the window is left (or the segment ends) before it is entered
+
     w.cM = c[0];
     w.cA = c[1];
     w.cB = c[2];
     w.dirM = dir[0];
     w.dirA = dir[1];
     w.dirB = dir[2];
-    w.sM = (int)(256 * den[0]);
-    w.sA = (int)(256 * den[1]);
-    w.sB = (int)(256 * den[2]);
+    w.sM = 256 * den[0];
+    w.sA = 256 * den[1];
+    w.sB = 256 * den[2];
     w.nsM = -w.sM;
     w.nsA = -w.sA;
-    w.dMA = (int)(num[0] * den[1] - num[1] * den[0]);
-    w.dMB = (int)(num[0] * den[2] - num[2] * den[0]);
-    w.dAB = (int)(num[1] * den[2] - num[2] * den[1]);
+    w.dMA = (int)((long long)num[0] * den[1] - (long long)num[1] * den[0]);
+    w.dMB = (int)((long long)num[0] * den[2] - (long long)num[2] * den[0]);
+    w.dAB = (int)((long long)num[1] * den[2] - (long long)num[2] * den[1]);
     // i first on equal t iff i moves up and j down: D_ij < t_ij with
     // t_ij = 1 then, else 0; j first iff D_ij > -t_ji.
-    const int rk0 = rank_of(dir[0]), rk1 = rank_of(dir[1]), rk2 = rank_of(dir[2]);
-    w.tMA = rk0 < rk1;
-    w.tAM = rk1 < rk0;
-    w.tMB = rk0 < rk2;
-    w.tBM = rk2 < rk0;
-    w.tAB = rk1 < rk2;
-    w.tBA = rk2 < rk1;
-    w.total = total;
-    w.nM = dim_of(g, M);
-    w.nA = dim_of(g, A);
-    w.nB = dim_of(g, B);
-    w.exitA = dir[1] > 0 ? w.nA : -1;
-    w.exitB = dir[2] > 0 ? w.nB : -1;
-    // a segment that starts with a minor axis already past the window has
-    // nothing left to count
-    if ((dir[1] > 0 ? c[1] >= w.nA : c[1] < 0) || (dir[2] > 0 ? c[2] >= w.nB : c[2] < 0)) return false;
+    w.tMA = rk[0] < rk[1];
+    w.tAM = rk[1] < rk[0];
+    w.tMB = rk[0] < rk[2];
+    w.tBM = rk[2] < rk[0];
+    w.tAB = rk[1] < rk[2];
+    w.tBA = rk[2] < rk[1];
+    w.rem = rem;
+    w.nM = n3[0];
+    w.nA = n3[1];
+    w.nB = n3[2];
     const int rr[3] = {g.rx, g.ry, g.rz};
     const uint32_t st[3] = {(uint32_t)g.ny * (uint32_t)g.nz, (uint32_t)g.nz, 1u};
     w.rM = sel3(rr, M);
@@ -461,8 +559,7 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     w.kM = sel3(st, M);
     w.kA = sel3(st, A);
     w.kB = sel3(st, B);
-    // power-of-two windows: the index fields (meaningful once the voxel is
-    // inside; the fields hold (c + r) mod n for any c, also before entry)
+    // power-of-two windows: the index fields of the first voxel (in the window)
     const uint32_t fm[3] = {((uint32_t)g.nx - 1u) * st[0], ((uint32_t)g.ny - 1u) * st[1], (uint32_t)g.nz - 1u};
     w.fmM = sel3(fm, M);
     w.fmA = sel3(fm, A);
@@ -514,8 +611,14 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
 
 // kPow2: every window of the launch has power-of-two extents (the index of
 // the current voxel is stepped, not recomputed).
+// Resident blocks per SM the walk is compiled for (registers per thread
+// = 65536 / (256 * this)): three keep its segment set-up in registers.
+#ifndef GVOM_MARCH_MIN_BLOCKS
+#define GVOM_MARCH_MIN_BLOCKS 3
+#endif
+
 template <bool kBatch, bool kSlot, bool kPow2>
-__global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
+__global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
     const unsigned long long total_items = *a1.w.item_count;
@@ -565,22 +668,19 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 live = walk_init(a1, qo1, b, (int)it.y, w);
             }
         }
-        // Visit the current voxel, then take the next crossing group,
-        // unless it moves the major axis past this segment. The ray's last
-        // voxel (no crossings left) is the endpoint voxel: no pass.
+        // Visit the current voxel (in the window by construction), then take
+        // the next crossing group; the segment's crossing budget ends the walk.
         // The step is branch-free: a lane that stops keeps stepping its
         // (no longer read) state until the whole warp has stopped.
         unsigned int item_n = 0;
         while (__any_sync(0xffffffffu, live)) {
-            live = live && w.total != 0;
-            const bool inside = live && (unsigned)w.cA < (unsigned)w.nA && (unsigned)w.cB < (unsigned)w.nB;
-            const uint32_t key = inside ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
+            const uint32_t key = live ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
             // runs of neighbouring lanes in the same voxel merge their
             // increments: the run's first lane adds the run's length
             bool boundary;
             if (kBatch) {
                 const unsigned long long kk =
-                    inside ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
+                    live ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
                 const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
                 boundary = lane == 0 || prev != kk;
             } else {
@@ -588,36 +688,31 @@ __global__ void __launch_bounds__(256, 4) k_march(const IngestArgs a1, const Ing
                 boundary = lane == 0 || prev != key;
             }
             const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-            if (inside && boundary && in_bounds(key, vmap, cnts)) {
+            if (live && boundary && in_bounds(key, vmap, cnts)) {
                 const unsigned int after = starts & ~((2u << lane) - 1u);
                 const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
                 atomicAdd(passes + key, run);
                 if (kSlot && spasses) atomicAdd(spasses + key, run);
             }
-            item_n += inside ? 1u : 0u;
+            item_n += live ? 1u : 0u;
             const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
             const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
             const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
-            // the major step past the segment's last slab ends the segment
-            live = live && !(gM && w.segM == 0);
             const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
-            w.segM = imad_s32(iM, -1, w.segM);
             if (kPow2) {
                 w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
                         ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
                         ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
             } else {
                 w.cM = imad_s32(iM, w.dirM, w.cM);
+                w.cA = imad_s32(iA, w.dirA, w.cA);
+                w.cB = imad_s32(iB, w.dirB, w.cB);
             }
-            w.cA = imad_s32(iA, w.dirA, w.cA);
-            w.cB = imad_s32(iB, w.dirB, w.cB);
             w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
             w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
             w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
-            w.total = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.total)));
-            // a minor axis past the window never comes back (steps are unit,
-            // so it passes the window exactly at its exit voxel)
-            live = live && w.cA != w.exitA && w.cB != w.exitB;
+            w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
+            live = live && w.rem > 0;
         }
         item_visits = item_n;
         if (kBatch && __any_sync(0xffffffffu, own_item != own)) {

@@ -367,3 +367,37 @@ def test_cone_values_on_hand_built_grids(gv, case):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(h.cpu().numpy(), ref["height"])
         np.testing.assert_array_equal(flags.cpu().numpy(), ref["flags"])
+
+
+@pytest.mark.parametrize("case", range(6))
+def test_exact_ties_on_voxel_corners_edges_and_faces(gv, case):
+    # res 0.25 m and coordinates on a 1/1024 m lattice make every quantised
+    # endpoint exact; the sensor on a voxel corner and endpoints on the
+    # quarter-voxel lattice make many crossings coincide (rays through voxel
+    # corners and along faces, diagonals through edges). Windows put the
+    # sensor inside, on the window's boundary, and outside, so rays enter
+    # and leave the window on such ties too. Passes and hits bit-exact.
+    rng = np.random.default_rng(700 + case)
+    dims = [(24, 20, 12), (16, 16, 16), (32, 8, 8), (12, 30, 10), (20, 20, 6), (9, 11, 13)][case]
+    params = oracle.OracleParams(nx=dims[0], ny=dims[1], nz=dims[2], res=0.25)
+    n = 6000
+    q = rng.integers(-40, 41, size=(n, 3)) * 64           # quarter voxels, in 1/256 voxel units
+    q[: n // 4] = rng.integers(-10, 11, size=(n // 4, 3)) * 256   # voxel corners
+    q[n // 4: n // 2, rng.integers(0, 3)] = 0             # rays in a coordinate plane
+    k = rng.integers(1, 9, size=(n // 8, 1)) * 256
+    q[n // 2: n // 2 + n // 8] = k * np.array([[1, 1, 1]]) * rng.choice([-1, 1], size=(n // 8, 3))  # body diagonals
+    pts = (q.astype(np.float64) / 256.0 * params.res).astype(np.float32)   # sensor frame, metres (exact)
+    sensor = np.array([0.5, -0.75, 0.25])                                   # a voxel corner (multiples of res)
+    T = np.array([[1.0, 0, 0, sensor[0]], [0, 1.0, 0, sensor[1]], [0, 0, 1.0, sensor[2]]])
+    sv = np.floor(sensor / params.res).astype(np.int64)
+    origins = [sv - np.array(dims) // 2, sv - np.array([0, 0, 0]), sv + np.array([3, -dims[1] - 2, 1]),
+               sv - np.array(dims) + 1, sv + np.array([-5, 2, -dims[2]]), sv + np.array([dims[0], 0, 0])]
+    o = origins[case]
+    om = oracle.OracleMap(params, tuple(int(v) for v in o))
+    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm.shift(tuple(int(v) for v in o))
+    om.ingest(pts, T)
+    gm.ingest(to_dev(pts), T)
+    compare_voxels(gm, om)
+    compare_stats(gm, om)
+    assert om.stats.pass_visits > 0 or case == 5
