@@ -674,13 +674,20 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
         // (no longer read) state until the whole warp has stopped.
         unsigned int item_n = 0;
         while (__any_sync(0xffffffffu, live)) {
-            const uint32_t key = live ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
+            // The voxel is in the window by construction. On power-of-two
+            // windows the masked index cannot leave the map anyway; on others
+            // the index is only formed for a voxel inside the window, so no
+            // access can leave the state arrays whatever the walk computes.
+            const bool visit = kPow2 ? live
+                                     : live && (unsigned)w.cM < (unsigned)w.nM && (unsigned)w.cA < (unsigned)w.nA &&
+                                           (unsigned)w.cB < (unsigned)w.nB;
+            const uint32_t key = visit ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
             // runs of neighbouring lanes in the same voxel merge their
             // increments: the run's first lane adds the run's length
             bool boundary;
             if (kBatch) {
                 const unsigned long long kk =
-                    live ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
+                    visit ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
                 const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
                 boundary = lane == 0 || prev != kk;
             } else {
@@ -688,13 +695,13 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
                 boundary = lane == 0 || prev != key;
             }
             const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-            if (live && boundary && in_bounds(key, vmap, cnts)) {
+            if (visit && boundary && in_bounds(key, vmap, cnts)) {
                 const unsigned int after = starts & ~((2u << lane) - 1u);
                 const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
                 atomicAdd(passes + key, run);
                 if (kSlot && spasses) atomicAdd(spasses + key, run);
             }
-            item_n += live ? 1u : 0u;
+            item_n += visit ? 1u : 0u;
             const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
             const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
             const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
