@@ -314,11 +314,12 @@ __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
 // voxel is ceil(P / 256) - 1.
 
 // q = floor(x / y) for 0 < y < 2^31 and |x / y| < 2^23: an FP32 estimate
-// corrected exactly with 64-bit integer remainders.
+// (reciprocal-based, a few units off at most) corrected exactly with 64-bit
+// integer remainders.
 __device__ __forceinline__ long long floor_div_small(long long x, long long y) {
     // x converted from its two 32-bit halves (FP32 pipe, not the FP64 one)
     const float xf = fmaf((float)(int)(x >> 32), 4294967296.0f, (float)(unsigned int)x);
-    long long q = (long long)floorf(__fdiv_rn(xf, (float)(int)y));
+    long long q = (long long)floorf(__fdividef(xf, (float)(int)y));
     long long r = x - q * y;
     while (r < 0) {
         q -= 1;

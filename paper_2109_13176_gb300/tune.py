@@ -15,7 +15,7 @@ import os
 import statistics
 import time
 
-CANDIDATES = [(L, blk, 0) for L in (6, 8, 12, 16, 24) for blk in (128, 256)]
+CANDIDATES = [(L, blk, 0) for L in (8, 12, 16, 24, 32, 48, 64) for blk in (128, 256)]
 
 
 def cache_path() -> str:

@@ -41,6 +41,6 @@ def test_cache_reuse_and_refresh(tmp_path, monkeypatch):
 def test_unwritable_cache_is_not_an_error(tmp_path, monkeypatch):
     (tmp_path / "afile").write_text("not a directory")
     monkeypatch.setenv("GVOM_TUNE_CACHE", str(tmp_path / "afile" / "t.json"))
-    run, _ = fake_run((6, 128, 0))
+    run, _ = fake_run((12, 128, 0))
     best, _ = tune.tuned("k", run, repeats=1)
-    assert best == (6, 128, 0)
+    assert best == (12, 128, 0)
