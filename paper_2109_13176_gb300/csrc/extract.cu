@@ -532,6 +532,9 @@ __device__ __forceinline__ float key_height(uint32_t k) {
 // tile-interior pixel to val.
 __device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int tile, int gx0, int gy0,
                                 bool along_x, int sgn, unsigned long long* Qbuf, float* val) {
+    // Hs rows are W + 1 floats apart and val rows tile + 1, so that the
+    // sweeps along y, whose lanes walk down a column, hit distinct banks
+    const int WP = W + 1, TP = tile + 1;
     const int lane = threadIdx.x & 31;
     const int nmaj = along_x ? p.g.nx : p.g.ny;
     const int g0 = along_x ? gx0 : gy0;  // global coordinate of tile row 0 along u
@@ -555,12 +558,12 @@ __device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, 
                 if (v + 1 < W) q = min(q, Qprev[v + 1]);
                 if (q != kNoGround && (q >> 32) < dmax >> 32) c = q + (1ull << 32);
             }
-            const float h = along_x ? Hs[u * W + v] : Hs[v * W + u];
+            const float h = along_x ? Hs[u * WP + v] : Hs[v * WP + u];
             const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
             Qcur[v] = min(own, c);
             const int iu = u - R, iv = v - R;
             if (iu >= 0 && iu < tile && iv >= 0 && iv < tile)
-                val[along_x ? iu * tile + iv : iv * tile + iu] =
+                val[along_x ? iu * TP + iv : iv * TP + iu] =
                     c != kNoGround ? key_height((uint32_t)c) : qnan;
         }
         __syncwarp();
@@ -572,7 +575,7 @@ __device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, 
 // height h0. The normal matrix is integer (exact, so is the singularity
 // test); the right-hand side and the solve are FP32.
 template <int kR>
-__device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* Hs, int W, int ci, int cj, float h0,
+__device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* Hs, int WP, int ci, int cj, float h0,
                                           float& sl, float& ro) {
     // kR > 0: compile-time radius (loops unrolled); kR == 0: run-time radius
     const int r = kR > 0 ? kR : p.slope_n / 2;
@@ -582,7 +585,7 @@ __device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* H
     for (int i = -r; i <= r; ++i)
 #pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
         for (int j = -r; j <= r; ++j) {
-            const float hv = Hs[(ci + i) * W + (cj + j)];
+            const float hv = Hs[(ci + i) * WP + (cj + j)];
             if (isnan(hv)) continue;
             const float z = hv - h0;
             n += 1;
@@ -613,7 +616,7 @@ __device__ __forceinline__ void plane_fit(const ExtractParams& p, const float* H
     for (int i = -r; i <= r; ++i)
 #pragma unroll (kR > 0 ? 2 * kR + 1 : 1)
         for (int j = -r; j <= r; ++j) {
-            const float hv = Hs[(ci + i) * W + (cj + j)];
+            const float hv = Hs[(ci + i) * WP + (cj + j)];
             if (isnan(hv)) continue;
             const float e = (hv - h0) - (a * (float)i + b * (float)j + c);
             sse += e * e;
@@ -633,18 +636,20 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     const int r = p.slope_n / 2;
     const int R = max(p.neg_max_px, r);
     const int W = tile + 2 * R;
+    const int WP = W + 1, TP = tile + 1;                // padded row strides (no bank conflicts down columns)
     const int warp = threadIdx.x >> 5;
     const int tt = tile * tile;
+    const int tv = tile * TP;                           // one direction's padded cone values
     unsigned long long* Qbufs = reinterpret_cast<unsigned long long*>(smem);  // 4 * 2W cone keys
-    float* Hs = smem + 16 * W;                          // W * W heights, NaN outside the grid
-    float* vals = Hs + W * W;                           // 4 * tile^2 cone values
+    float* Hs = smem + 16 * W;                          // W rows of WP heights, NaN outside the grid
+    float* vals = Hs + W * WP;                          // 4 * tile rows of TP cone values
     const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
 
     for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
         const int i = t / W, j = t % W;
         const int gx = gx0 + i, gy = gy0 + j;
-        Hs[t] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
+        Hs[i * WP + j] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
     }
     __syncthreads();
 
@@ -652,21 +657,21 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     // the planes; with four, all fit, then each sweeps one cone
     const bool split = flags && blockDim.x >= 256;
     const int fit0 = split ? 128 : 0;
-    if (!split || warp >= 4) {
+    if ((slope || rough) && (!split || warp >= 4)) {
         for (int t = (int)threadIdx.x - fit0; t < tt; t += (int)blockDim.x - fit0) {
             const int li = t / tile, lj = t % tile;
             const int cx = tx0 + li, cy = ty0 + lj;
             if (cx >= nx || cy >= ny) continue;
             const int ci = li + R, cj = lj + R;
-            const float h0 = Hs[ci * W + cj];
+            const float h0 = Hs[ci * WP + cj];
             float sl = qnan, ro = qnan;
             if (!isnan(h0)) {
                 if (r == 2)
-                    plane_fit<2>(p, Hs, W, ci, cj, h0, sl, ro);  // the default 5 x 5 window
+                    plane_fit<2>(p, Hs, WP, ci, cj, h0, sl, ro);  // the default 5 x 5 window
                 else if (r == 1)
-                    plane_fit<1>(p, Hs, W, ci, cj, h0, sl, ro);
+                    plane_fit<1>(p, Hs, WP, ci, cj, h0, sl, ro);
                 else
-                    plane_fit<0>(p, Hs, W, ci, cj, h0, sl, ro);
+                    plane_fit<0>(p, Hs, WP, ci, cj, h0, sl, ro);
             }
             const size_t o = (size_t)cx * ny + cy;
             if (slope) slope[o] = sl;
@@ -676,18 +681,18 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     if (flags) {
         if (warp < 4)
             cone_sweep_warp(p, Hs, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
-                            vals + warp * tt);
+                            vals + warp * tv);
         __syncthreads();
         for (int t = threadIdx.x; t < tt; t += blockDim.x) {
             const int li = t / tile, lj = t % tile;
             const int cx = tx0 + li, cy = ty0 + lj;
             if (cx >= nx || cy >= ny) continue;
-            if (!isnan(Hs[(li + R) * W + (lj + R)])) continue;
+            if (!isnan(Hs[(li + R) * WP + (lj + R)])) continue;
             int nf = 0;
             float lo = 0.f, hi = 0.f;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const float v = vals[c * tt + t];
+                const float v = vals[c * tv + li * TP + lj];
                 if (isnan(v)) continue;
                 lo = nf ? fminf(lo, v) : v;
                 hi = nf ? fmaxf(hi, v) : v;
@@ -770,7 +775,8 @@ __global__ void __launch_bounds__(kPxBlockBatch, 8) k_slope_negative_batch(Batch
 
 size_t slope_negative_smem_tile(int R, int tile) {
     const int W = tile + 2 * R;
-    return sizeof(unsigned long long) * 8 * (size_t)W + sizeof(float) * ((size_t)W * W + 4 * tile * tile);
+    return sizeof(unsigned long long) * 8 * (size_t)W +
+           sizeof(float) * ((size_t)W * (W + 1) + 4 * (size_t)tile * (tile + 1));
 }
 
 
