@@ -799,21 +799,11 @@ __device__ __forceinline__ void cone_strip(const ExtractParams& p, const float* 
         }
         const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
         Q[st & 1][t] = min(own, c);
-        // the cone value replaces the height this thread just read (each
-        // cell of Hs is read and written by its own thread only)
-        if (out_col && u >= u_lo && u < u_hi) Hs[(u - u_min) * TP + t] = c != kNoGround ? key_height((uint32_t)c) : qnan;
+        if (out_col && u >= u_lo && u < u_hi) {
+            const size_t o = along_x ? (size_t)u * ny + v : (size_t)v * ny + u;
+            vout[o] = c != kNoGround ? key_height((uint32_t)c) : qnan;
+        }
         __syncthreads();
-    }
-    // the output block, written with consecutive threads on consecutive
-    // addresses (along v for the x cones, along u for the y cones)
-    const int B = strip_out(p), rows = u_hi - u_lo;
-    for (int i = t; i < rows * B; i += kStripThreads) {
-        const int row = along_x ? i / B : i % rows;
-        const int col = along_x ? i % B : i / rows;
-        const int vv = v0 + R + col, uu = u_lo + row;
-        if (vv >= nv) continue;
-        const size_t o = along_x ? (size_t)uu * ny + vv : (size_t)vv * ny + uu;
-        vout[o] = Hs[(uu - u_min) * TP + R + col];
     }
 }
 
