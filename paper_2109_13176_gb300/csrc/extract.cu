@@ -747,15 +747,14 @@ __host__ __device__ __forceinline__ void strip_counts(const ExtractParams& p, in
 // output pixel to vals[dir * nx * ny + x * ny + y].
 __device__ __forceinline__ void cone_strip(const ExtractParams& p, const float* __restrict__ height,
                                            float* __restrict__ vals, int dir, int band, int chunk,
-                                           unsigned char* sm) {
+                                           unsigned long long (*Q)[kStripThreads]) {
     const int nx = p.g.nx, ny = p.g.ny;
     const bool along_x = dir < 2;
     const int sgn = (dir & 1) ? -1 : 1;
     const int nu = along_x ? nx : ny, nv = along_x ? ny : nx;
     const int R = p.neg_max_px;
     const int t = threadIdx.x;
-    const int v0 = band * strip_out(p) - R;
-    const int v = v0 + t;
+    const int v = band * strip_out(p) - R + t;
     const bool v_in = v >= 0 && v < nv;
     const bool out_col = t >= R && t < kStripThreads - R && v_in;
     const int u_lo = chunk * kStripRows, u_hi = min(nu, u_lo + kStripRows);  // output rows [u_lo, u_hi)
@@ -763,31 +762,19 @@ __device__ __forceinline__ void cone_strip(const ExtractParams& p, const float* 
     // order (within the grid); the row before it counts as no ground
     const int u_first = sgn > 0 ? min(nu - 1, u_hi - 1 + R) : max(0, u_lo - R);
     const int nsteps = sgn > 0 ? u_first - u_lo + 1 : u_hi - u_first;
-    const int u_min = sgn > 0 ? u_lo : u_first;  // the strip's rows are [u_min, u_min + nsteps)
     const unsigned long long dmax = (unsigned long long)R << 32;
     const float qnan = __int_as_float(0x7fffffff);
     float* vout = vals + (size_t)dir * nx * ny;
-    unsigned long long (*Q)[kStripThreads] = reinterpret_cast<unsigned long long (*)[kStripThreads]>(sm);
-    // the strip's heights, staged once (all loads in flight together):
-    // Hs[(u - u_min) * TP + t], rows padded to TP = kStripThreads + 1
-    constexpr int TP = kStripThreads + 1;
-    float* Hs = reinterpret_cast<float*>(sm + sizeof(unsigned long long) * 2 * kStripThreads);
-    const int cells = nsteps * kStripThreads;
-    for (int i = t; i < cells; i += kStripThreads) {
-        // consecutive threads read consecutive addresses: along v for the x
-        // cones (rows of the height map), along u for the y cones
-        const int row = along_x ? i / kStripThreads : i % nsteps;
-        const int col = along_x ? i % kStripThreads : i / nsteps;
-        const int vv = v0 + col, uu = u_min + row;
-        float h = qnan;
-        if (vv >= 0 && vv < nv)
-            h = along_x ? __ldg(height + (size_t)uu * ny + vv) : __ldg(height + (size_t)vv * ny + uu);
-        Hs[row * TP + col] = h;
-    }
-    __syncthreads();
+    // the height of this thread's cell in row u
+    auto own_height = [&](int u) -> float {
+        if (!v_in) return qnan;
+        return along_x ? __ldg(height + (size_t)u * ny + v) : __ldg(height + (size_t)v * ny + u);
+    };
+    float h_next = own_height(u_first);
     for (int st = 0; st < nsteps; ++st) {
         const int u = u_first - sgn * st;
-        const float h = Hs[(u - u_min) * TP + t];
+        const float h = h_next;
+        if (st + 1 < nsteps) h_next = own_height(u - sgn);  // the next row's load overlaps this step
         const unsigned long long* Qprev = Q[(st + 1) & 1];
         unsigned long long c = kNoGround;
         const int un = u + sgn;  // the ring-1 row, swept in the previous step
@@ -805,11 +792,6 @@ __device__ __forceinline__ void cone_strip(const ExtractParams& p, const float* 
         }
         __syncthreads();
     }
-}
-
-size_t cone_strip_smem(const ExtractParams& p) {
-    return sizeof(unsigned long long) * 2 * kStripThreads +
-           sizeof(float) * (size_t)(kStripRows + p.neg_max_px) * (kStripThreads + 1);
 }
 
 // Plane fits of one kFitTile x kFitTile tile (its halo is the fit radius).
@@ -869,7 +851,8 @@ __global__ void __launch_bounds__(kStripThreads) k_cones_fits(ExtractParams p, c
             int bands, chunks;
             strip_counts(p, dir, &bands, &chunks);
             if (local < bands * chunks) {
-                cone_strip(p, height, vals, dir, local % bands, local / bands, px_sm);
+                cone_strip(p, height, vals, dir, local % bands, local / bands,
+                           reinterpret_cast<unsigned long long (*)[kStripThreads]>(px_sm));
                 break;
             }
             local -= bands * chunks;
@@ -1153,7 +1136,7 @@ cudaError_t launch_pixel_strips(const ExtractParams& p, const float* height, flo
     const int fits = (slope || rough) ? 1 : 0;
     const long long n_fit =
         fits ? (long long)((p.g.nx + kFitTile - 1) / kFitTile) * ((p.g.ny + kFitTile - 1) / kFitTile) : 0;
-    const size_t smem_cone = flags ? cone_strip_smem(p) : 0;
+    const size_t smem_cone = sizeof(unsigned long long) * 2 * kStripThreads;
     const size_t smem_fit = fits ? fit_tile_smem(p) : 0;
     const size_t smem = smem_cone > smem_fit ? smem_cone : smem_fit;
     if (smem > 48 * 1024) {
