@@ -213,7 +213,6 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->s.minz, sizeof(float) * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&m->cone_scratch, sizeof(float) * 4 * (size_t)cfg->nx * cfg->ny);
     if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(m->w.item_count, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&m->lut_counts, sizeof(unsigned int) * (size_t)gvom::lut_blocks(V));
@@ -245,7 +244,6 @@ void gvom_destroy(gvom_map* m) {
     cudaFree(m->s.minz);
     cudaFree(m->s.counters);
     cudaFree(m->height_scratch);
-    cudaFree(m->cone_scratch);
     cudaFree(m->w.rays);
     cudaFree(m->w.items);
     cudaFree(m->w.item_count);
@@ -377,8 +375,7 @@ int gvom_extract_maps(gvom_map* m, const gvom_maps_out* out, gvom_stream_t strea
     cudaError_t e = gvom::launch_columns(m->s, p, height, out->density_dev, out->flags_dev, st);
     if (e != cudaSuccess) return cuda_status(e);
     if (out->slope_dev || out->roughness_dev || out->flags_dev)
-        e = gvom::launch_pixel_strips(p, height, m->cone_scratch, out->slope_dev, out->roughness_dev, out->flags_dev,
-                                      st);
+        e = gvom::launch_slope_negative(p, height, out->slope_dev, out->roughness_dev, out->flags_dev, st);
     return cuda_status(e);
 }
 

@@ -714,177 +714,6 @@ __global__ void __launch_bounds__(kPxBlock, 4)
     pdl_done();
 }
 
-// ---- strip form of the pixel pass (one map with cone scratch) -------------
-//
-// The tile form above sweeps each cone direction over a tile plus a halo of
-// the search distance R on every side: with R = 20 px a 24-px tile costs
-// about five cell updates per pixel and direction. Here each block sweeps one
-// direction over a strip: kStripThreads cells across (one per thread; the
-// middle kStripThreads - 2R are output, the R on each side are halo) and
-// kStripRows output rows along the sweep, started R rows early -- about 1.6
-// updates per pixel. The plane fits run in the same launch, in separate
-// blocks, on tiles whose halo is only the fit's radius. A third kernel then
-// combines each undefined pixel's four cone values into bit 3 of flags.
-
-constexpr int kStripThreads = 256;
-constexpr int kStripRows = 32;
-constexpr int kFitTile = 32;
-
-__host__ __device__ __forceinline__ int strip_out(const ExtractParams& p) { return kStripThreads - 2 * p.neg_max_px; }
-
-__host__ __device__ __forceinline__ void strip_counts(const ExtractParams& p, int dir, int* bands, int* chunks) {
-    const int nu = dir < 2 ? p.g.nx : p.g.ny, nv = dir < 2 ? p.g.ny : p.g.nx;
-    *bands = (nv + strip_out(p) - 1) / strip_out(p);
-    *chunks = (nu + kStripRows - 1) / kStripRows;
-}
-
-// One direction over one strip. dir 0 / 1: cones along +x / -x (u = x,
-// v = y); dir 2 / 3: along +y / -y (u = y, v = x). The cone toward +u
-// depends on row u + 1, so it is swept from high u to low u (and the other
-// way for -u). A cell's state is min(own key, cone state), the cone state
-// the minimum over its three ring-1 cells of their states one ring further,
-// as in cone_sweep_warp. Writes the cone value (NaN if none) of every
-// output pixel to vals[dir * nx * ny + x * ny + y].
-__device__ __forceinline__ void cone_strip(const ExtractParams& p, const float* __restrict__ height,
-                                           float* __restrict__ vals, int dir, int band, int chunk,
-                                           unsigned long long (*Q)[kStripThreads]) {
-    const int nx = p.g.nx, ny = p.g.ny;
-    const bool along_x = dir < 2;
-    const int sgn = (dir & 1) ? -1 : 1;
-    const int nu = along_x ? nx : ny, nv = along_x ? ny : nx;
-    const int R = p.neg_max_px;
-    const int t = threadIdx.x;
-    const int v = band * strip_out(p) - R + t;
-    const bool v_in = v >= 0 && v < nv;
-    const bool out_col = t >= R && t < kStripThreads - R && v_in;
-    const int u_lo = chunk * kStripRows, u_hi = min(nu, u_lo + kStripRows);  // output rows [u_lo, u_hi)
-    // first row of the sweep: R rows before the first output row in sweep
-    // order (within the grid); the row before it counts as no ground
-    const int u_first = sgn > 0 ? min(nu - 1, u_hi - 1 + R) : max(0, u_lo - R);
-    const int nsteps = sgn > 0 ? u_first - u_lo + 1 : u_hi - u_first;
-    const unsigned long long dmax = (unsigned long long)R << 32;
-    const float qnan = __int_as_float(0x7fffffff);
-    float* vout = vals + (size_t)dir * nx * ny;
-    // the height of this thread's cell in row u
-    auto own_height = [&](int u) -> float {
-        if (!v_in) return qnan;
-        return along_x ? __ldg(height + (size_t)u * ny + v) : __ldg(height + (size_t)v * ny + u);
-    };
-    float h_next = own_height(u_first);
-    for (int st = 0; st < nsteps; ++st) {
-        const int u = u_first - sgn * st;
-        const float h = h_next;
-        if (st + 1 < nsteps) h_next = own_height(u - sgn);  // the next row's load overlaps this step
-        const unsigned long long* Qprev = Q[(st + 1) & 1];
-        unsigned long long c = kNoGround;
-        const int un = u + sgn;  // the ring-1 row, swept in the previous step
-        if (st > 0 && un >= 0 && un < nu) {
-            unsigned long long q = Qprev[t];
-            if (t > 0) q = min(q, Qprev[t - 1]);
-            if (t + 1 < kStripThreads) q = min(q, Qprev[t + 1]);
-            if (q != kNoGround && q < dmax) c = q + (1ull << 32);
-        }
-        const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
-        Q[st & 1][t] = min(own, c);
-        if (out_col && u >= u_lo && u < u_hi) {
-            const size_t o = along_x ? (size_t)u * ny + v : (size_t)v * ny + u;
-            vout[o] = c != kNoGround ? key_height((uint32_t)c) : qnan;
-        }
-        __syncthreads();
-    }
-}
-
-// Plane fits of one kFitTile x kFitTile tile (its halo is the fit radius).
-__device__ __forceinline__ void fit_tile(const ExtractParams& p, const float* __restrict__ height,
-                                         float* __restrict__ slope, float* __restrict__ rough, int tile_idx,
-                                         float* Hs) {
-    const int nx = p.g.nx, ny = p.g.ny;
-    const int r = p.slope_n / 2;
-    const int W = kFitTile + 2 * r, WP = W + 1;
-    const int tiles_y = (ny + kFitTile - 1) / kFitTile;
-    const int tx0 = (tile_idx / tiles_y) * kFitTile, ty0 = (tile_idx % tiles_y) * kFitTile;
-    const int gx0 = tx0 - r, gy0 = ty0 - r;
-    const float qnan = __int_as_float(0x7fffffff);
-    for (int i = threadIdx.x; i < W * W; i += blockDim.x) {
-        const int a = i / W, b = i % W;
-        const int gx = gx0 + a, gy = gy0 + b;
-        Hs[a * WP + b] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? __ldg(height + (size_t)gx * ny + gy) : qnan;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kFitTile * kFitTile; i += blockDim.x) {
-        const int li = i / kFitTile, lj = i % kFitTile;
-        const int cx = tx0 + li, cy = ty0 + lj;
-        if (cx >= nx || cy >= ny) continue;
-        const int ci = li + r, cj = lj + r;
-        const float h0 = Hs[ci * WP + cj];
-        float sl = qnan, ro = qnan;
-        if (!isnan(h0)) {
-            if (r == 2)
-                plane_fit<2>(p, Hs, WP, ci, cj, h0, sl, ro);
-            else if (r == 1)
-                plane_fit<1>(p, Hs, WP, ci, cj, h0, sl, ro);
-            else
-                plane_fit<0>(p, Hs, WP, ci, cj, h0, sl, ro);
-        }
-        const size_t o = (size_t)cx * ny + cy;
-        if (slope) slope[o] = sl;
-        if (rough) rough[o] = ro;
-    }
-}
-
-size_t fit_tile_smem(const ExtractParams& p) {
-    const int W = kFitTile + 2 * (p.slope_n / 2);
-    return sizeof(float) * (size_t)W * (W + 1);
-}
-
-// Blocks [0, n_cone) sweep cone strips (four directions), the rest fit
-// planes; the two kinds share nothing but the height map.
-__global__ void __launch_bounds__(kStripThreads) k_cones_fits(ExtractParams p, const float* __restrict__ height,
-                                                             float* __restrict__ vals, float* __restrict__ slope,
-                                                             float* __restrict__ rough, int n_cone, int fits) {
-    pdl_wait();
-    extern __shared__ __align__(16) unsigned char px_sm[];
-    const int b = blockIdx.x;
-    if (b < n_cone) {
-        int dir = 0, local = b;
-        for (; dir < 4; ++dir) {
-            int bands, chunks;
-            strip_counts(p, dir, &bands, &chunks);
-            if (local < bands * chunks) {
-                cone_strip(p, height, vals, dir, local % bands, local / bands,
-                           reinterpret_cast<unsigned long long (*)[kStripThreads]>(px_sm));
-                break;
-            }
-            local -= bands * chunks;
-        }
-    } else if (fits) {
-        fit_tile(p, height, slope, rough, b - n_cone, reinterpret_cast<float*>(px_sm));
-    }
-    pdl_done();
-}
-
-// Bit 3 of flags from the four cone values of each undefined pixel.
-__global__ void __launch_bounds__(256) k_cone_combine(ExtractParams p, const float* __restrict__ height,
-                                                       const float* __restrict__ vals, uint8_t* __restrict__ flags) {
-    pdl_wait();
-    const size_t n = (size_t)p.g.nx * p.g.ny;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        if (!isnan(__ldg(height + i))) continue;
-        int nf = 0;
-        float lo = 0.f, hi = 0.f;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float v = __ldg(vals + (size_t)c * n + i);
-            if (isnan(v)) continue;
-            lo = nf ? fminf(lo, v) : v;
-            hi = nf ? fmaxf(hi, v) : v;
-            nf += 1;
-        }
-        if (nf >= 2 && exceeds(hi, lo, p.neg_thresh)) flags[i] |= 8u;
-    }
-    pdl_done();
-}
-
 // ---- batched maps ----------------------------------------------------------
 
 __device__ __forceinline__ int find_map_x(const long long* __restrict__ prefix, int B, long long u) {
@@ -1122,42 +951,6 @@ cudaError_t launch_scatter_voxels(const MapState& s, const Geom& g, const uint32
     count_launch();
     k_scatter_voxels<<<(unsigned)blocks, 256, 0, st>>>(s, g, hits, passes, minz);
     return cudaGetLastError();
-}
-
-cudaError_t launch_pixel_strips(const ExtractParams& p, const float* height, float* cone_vals, float* slope,
-                                float* rough, uint8_t* flags, cudaStream_t st) {
-    int n_cone = 0;
-    if (flags)
-        for (int dir = 0; dir < 4; ++dir) {
-            int bands, chunks;
-            strip_counts(p, dir, &bands, &chunks);
-            n_cone += bands * chunks;
-        }
-    const int fits = (slope || rough) ? 1 : 0;
-    const long long n_fit =
-        fits ? (long long)((p.g.nx + kFitTile - 1) / kFitTile) * ((p.g.ny + kFitTile - 1) / kFitTile) : 0;
-    const size_t smem_cone = sizeof(unsigned long long) * 2 * kStripThreads;
-    const size_t smem_fit = fits ? fit_tile_smem(p) : 0;
-    const size_t smem = smem_cone > smem_fit ? smem_cone : smem_fit;
-    if (smem > 48 * 1024) {
-        static std::atomic<int> cache[64];
-        const cudaError_t e = allow_smem((const void*)k_cones_fits, cache, smem);
-        if (e != cudaSuccess) return e;
-    }
-    if (n_cone + n_fit > 0) {
-        count_launch();
-        const cudaError_t e = launch_pdl(k_cones_fits, dim3((unsigned)(n_cone + n_fit)), dim3(kStripThreads), smem, st,
-                                         p, height, cone_vals, slope, rough, n_cone, fits);
-        if (e != cudaSuccess || !flags) return e;
-    }
-    if (!flags) return cudaSuccess;
-    const long long n = (long long)p.g.nx * p.g.ny;
-    long long blocks = (n + 255) / 256;
-    const long long cap = (long long)sm_count() * 8;
-    if (blocks > cap) blocks = cap;
-    count_launch();
-    return launch_pdl(k_cone_combine, dim3((unsigned)blocks), dim3(256), 0, st, p, height, (const float*)cone_vals,
-                      flags);
 }
 
 cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,

@@ -245,11 +245,6 @@ cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* hei
                            uint8_t* flags, cudaStream_t st);
 cudaError_t launch_slope_negative(const ExtractParams& p, const float* height, float* slope, float* rough,
                                   uint8_t* flags, cudaStream_t st);
-// The strip form of the same pass (cone sweeps over strips and plane fits in
-// one launch, then the per-pixel combination): needs cone_vals, 4 * nx * ny
-// floats of scratch.
-cudaError_t launch_pixel_strips(const ExtractParams& p, const float* height, float* cone_vals, float* slope,
-                                float* rough, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_gather_voxels(const MapState& s, const Geom& g, uint32_t* hits, uint32_t* passes, float* minz,
                                  cudaStream_t st);
 cudaError_t launch_scatter_voxels(const MapState& s, const Geom& g, const uint32_t* hits, const uint32_t* passes,
@@ -270,7 +265,6 @@ struct gvom_map {
     gvom::MapState s;
     gvom::RayScratch w;     // per-scan ray records and segment work list
     float* height_scratch;  // nx * ny, used when the caller asks for no height
-    float* cone_scratch;    // 4 * nx * ny: each pixel's cone value per direction (the strip pixel pass)
     unsigned int* lut_counts;  // per-block counts of the lookup-table export
     struct gvom_batch* multi;  // tables for gvom_ingest_multi (created on first use)
     int buf_head;                    // ring slot of the next scan
