@@ -124,6 +124,8 @@ def load_library():
             "gvom_batch_step": ([vp, P(vp), i32, P(ctypes.c_double), P(vp), P(i64), i32, P(ctypes.c_double),
                                  P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_microbench_red": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
+            "gvom_microbench_red_coalesced": ([vp, i64, i64, ctypes.c_uint32, vp], ctypes.c_int),
+            "gvom_set_walk_marker": ([vp, vp], ctypes.c_int),
             "gvom_extract_maps_noalloc": ([P(gvom_config), vp, vp, vp, P(gvom_maps_out), vp], ctypes.c_int),
             "gvom_kernel_launches": ([], ctypes.c_int64),
             "gvom_ingest_multi": ([vp, i32, P(vp), P(i64), i32, P(ctypes.c_double), vp], ctypes.c_int),
@@ -513,6 +515,18 @@ class MapBatch:
 def gvom_microbench_red(buf, ops: int, seed: int = 1, stream=None) -> None:
     _check(load_library().gvom_microbench_red(buf.data_ptr(), buf.numel(), int(ops), seed & 0xffffffff,
                                               _stream_handle(stream)), "gvom_microbench_red")
+
+
+def gvom_microbench_red_coalesced(buf, ops: int, seed: int = 1, stream=None) -> None:
+    _check(load_library().gvom_microbench_red_coalesced(buf.data_ptr(), buf.numel(), int(ops), seed & 0xffffffff,
+                                                        _stream_handle(stream)), "gvom_microbench_red_coalesced")
+
+
+def gvom_set_walk_marker(handle: int, event=None) -> None:
+    """event: a torch.cuda.Event (or None to turn the marker off); see
+    include/gvom_microbench.h."""
+    ptr = None if event is None else ctypes.c_void_p(int(event.cuda_event))
+    _check(load_library().gvom_set_walk_marker(handle, ptr), "gvom_set_walk_marker")
 
 
 def gvom_kernel_launches() -> int:

@@ -350,7 +350,13 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     shape.blocks_per_sm = m->tune.march_blocks_per_sm;
     m->scans += 1;
     m->points_in += n;
-    return cuda_status(gvom::launch_ingest(a, shape, (cudaStream_t)stream));
+    return cuda_status(gvom::launch_ingest(a, shape, (cudaStream_t)stream, m->walk_marker));
+}
+
+int gvom_set_walk_marker(gvom_map* m, void* cuda_event) {
+    if (!m) return GVOM_ERR_INVALID_ARG;
+    m->walk_marker = (cudaEvent_t)cuda_event;
+    return GVOM_OK;
 }
 
 int gvom_update(gvom_map* m, const double vehicle_xyz[3], const float* pts_dev, int64_t n, int32_t stride,

@@ -238,7 +238,9 @@ cudaError_t launch_init_state(const MapState& s, long long V, cudaStream_t st);
 // recomputing the lowest return where an emptied slot held it.
 cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_t st);
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st);
-cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st);
+// marker: a caller event recorded between the per-point pass and the walk (or null).
+cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st,
+                          cudaEvent_t marker = nullptr);
 // Segments a ray of the given window can have at most, for segment length L.
 long long max_segments_per_ray(const Geom& g, int seg_len);
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density,
@@ -270,6 +272,7 @@ struct gvom_map {
     int buf_head;                    // ring slot of the next scan
     unsigned long long buf_occupied; // ring slots holding a scan
     gvom_tuning tune;
+    cudaEvent_t walk_marker;         // gvom_set_walk_marker (null: none)
     long long scans;
     long long points_in;
     int device;

@@ -1175,13 +1175,14 @@ cudaError_t launch_march_one(const IngestArgs& a, const MarchShape& shape, cudaS
                       0, st, a, none, no_sensors);
 }
 
-cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
+cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st, cudaEvent_t marker) {
     if (a.n <= 0) return cudaSuccess;
     // the work list is empty here: the previous scan's walk emptied it
     const long long blocks = (a.n + kRaysBlock - 1) / kRaysBlock;
     count_launch();
     cudaError_t e = launch_pdl(k_rays, dim3((unsigned)blocks), dim3(kRaysBlock), 0, st, a);
     if (e != cudaSuccess) return e;
+    if (marker && (e = cudaEventRecord(marker, st)) != cudaSuccess) return e;
     count_launch();
     const bool pow2 = pow2_window(a.g);
     if (a.slot >= 0)
