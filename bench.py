@@ -671,6 +671,8 @@ def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=
     nt = min(4, ns)
     tuning, tune_entry = tune.tune_map(gmap, dev_pts[:nt], [s.T_ws for s in scans[:nt]],
                                        [s.vehicle_xyz for s in scans[:nt]], flush=flush, refresh=args.retune)
+    # extraction shapes, on the state those scans left
+    ext_tuning, ext_entry = tune.tune_extract(gmap, out, flush=flush, refresh=args.retune)
     gmap.reset((0, 0, 0))
     gmap.reset_stats()
 
@@ -713,7 +715,8 @@ def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=
          "shift_ms": [e[0].elapsed_time(e[1]) for e in ev],
          "rays": st1["rays_valid"] - st0["rays_valid"], "visits": st1["pass_visits"] - st0["pass_visits"],
          "hits": st1["hits_in_window"] - st0["hits_in_window"], "launches": launches,
-         "tuning": tuning, "tune_entry": tune_entry, "cfg": cfg, "n_scans": ns}
+         "tuning": tuning, "tune_entry": tune_entry, "ext_tuning": ext_tuning, "ext_entry": ext_entry,
+         "cfg": cfg, "n_scans": ns}
     r["total_s"] = sum(r["step_ms"]) * 1e-3
 
     # the walk by itself: a caller event recorded by the library between the
@@ -762,10 +765,34 @@ def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    gc.enable()
     st2 = gmap.stats()
     r.update({"e2e_ms": e2e_ms, "e2e_s": sum(e2e_ms) * 1e-3, "rays_e2e": st2["rays_valid"] - st1["rays_valid"],
               "h2d": int(h2d), "d2h": int(packed_dev.numel())})
+
+    # end to end through the asynchronous pipeline (gvom_pipeline_*): the same
+    # scans from pinned host memory, every product back in pinned host
+    # memory, with the copies of neighbouring scans overlapping the compute;
+    # host wall clock from the first submit to the last scan's products
+    pipe = gv.Pipeline(gmap, max(int(p.shape[0]) for p in host_pts))
+    houts = [pipe.alloc_host_outs() for _ in range(3)]
+    tk = 0
+    for i in range(6):
+        s = scans[i % ns]
+        tk = pipe.submit(s.vehicle_xyz, host_pts[i % ns], s.T_ws, houts[i % 3])
+    pipe.wait(tk)
+    torch.cuda.synchronize()
+    p0 = gmap.stats()["rays_valid"]
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        k = args.warmup + i
+        s = scans[k % ns]
+        tk = pipe.submit(s.vehicle_xyz, host_pts[k % ns], s.T_ws, houts[i % 3])
+    pipe.wait(tk)
+    wall = time.perf_counter() - t0
+    gc.enable()
+    r.update({"e2e_pipe_s": wall, "rays_e2e_pipe": gmap.stats()["rays_valid"] - p0, "e2e_pipe_steps": e2e_steps,
+              "d2h_pipe": int(sum(v.numel() * v.element_size() for v in houts[0].values()))})
+    pipe.close()
     gmap.close()
     return r
 
@@ -814,10 +841,19 @@ def extract_roofline(r, ms, hbm_peak, peak_kind):
 
 
 def e2e_object(r):
-    return {"value": r["rays_e2e"] / r["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
-            "d2h_bytes_per_step": r["d2h"], "ms_per_step_p50": statistics.median(r["e2e_ms"]),
-            "ms_per_step_p99": sorted(r["e2e_ms"])[int(0.99 * (len(r["e2e_ms"]) - 1))], "steps": len(r["e2e_ms"]),
-            "call": "pinned H2D copy, gvom_update_extract, one D2H copy of the packed products, per step"}
+    """End to end through the public API: the asynchronous pipeline (the
+    value), with one synchronised scan at a time beside it."""
+    return {"value": r["rays_e2e_pipe"] / r["e2e_pipe_s"], "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+            "d2h_bytes_per_step": r["d2h_pipe"], "ms_per_step": 1e3 * r["e2e_pipe_s"] / r["e2e_pipe_steps"],
+            "steps": r["e2e_pipe_steps"],
+            "call": "gvom_pipeline_submit per scan (pinned host points in; shift, ingest and every product; each "
+                    "scan's products back in pinned host memory), three scans in flight, host wall clock from the "
+                    "first submit to the last scan's products; no L2 flush (scans overlap)",
+            "serial": {"value": r["rays_e2e"] / r["e2e_s"], "ms_per_step_p50": statistics.median(r["e2e_ms"]),
+                       "ms_per_step_p99": sorted(r["e2e_ms"])[int(0.99 * (len(r["e2e_ms"]) - 1))],
+                       "d2h_bytes_per_step": r["d2h"], "steps": len(r["e2e_ms"]),
+                       "call": "one scan at a time: pinned H2D copy, gvom_update_extract, one D2H copy of the "
+                               "packed products, synchronised, CUDA events per scan"}}
 
 
 def plain_summary(args, r, workload, red_peak, red_coalesced, hbm_peak, peak_kind):
@@ -838,7 +874,8 @@ def plain_summary(args, r, workload, red_peak, red_coalesced, hbm_peak, peak_kin
             "roofline_extract": extract_roofline(r, ms, hbm_peak, peak_kind),
             "e2e": e2e_object(r), "gpu_launches_per_step": r["launches"] / steps,
             "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1],
-                       "march_blocks_per_sm": r["tuning"][2]},
+                       "march_blocks_per_sm": r["tuning"][2], "px_tile": r["ext_tuning"][0],
+                       "col_shape": r["ext_tuning"][1]},
             "l2": L2_NOTE}
 
 
@@ -980,7 +1017,7 @@ def main():
     clocks = ClockSampler(local)
     r = measure_plain(args, gv, tune, torch, inputs, flush, stream, world=world, clocks=clocks,
                       e2e_steps=max(args.steps, 200))
-    total_s, e2e_s, rays, rays_e2e = r["total_s"], r["e2e_s"], r["rays"], r["rays_e2e"]
+    total_s, e2e_s, rays, rays_e2e = r["total_s"], r["e2e_pipe_s"], r["rays"], r["rays_e2e_pipe"]
     if world > 1:
         (total_s, e2e_s), (rays, rays_e2e) = reduce_over_ranks([total_s, e2e_s], [rays, rays_e2e], "cuda")
 
@@ -1015,8 +1052,10 @@ def main():
     if not args.no_next_rows:
         seq_cfg, seq_scans = seq_inputs
         seq_tuning = r["tuning"] if main_wl == "sequence" else (
-            tuple(other["tuning"].values()) if other else (16, 256, 0))
-        seq_e2e = (rays_e2e / e2e_s) if main_wl == "sequence" else (other["e2e"]["value"] if other else None)
+            tuple(other["tuning"][k] for k in ("seg_len", "march_block", "march_blocks_per_sm")) if other
+            else (16, 256, 0))
+        seq_e2e = (r["rays_e2e"] / r["e2e_s"]) if main_wl == "sequence" else (
+            other["e2e"]["serial"]["value"] if other else None)
         next_rows = run_next_rows(args, gv, torch, seq_cfg, seq_scans, seq_tuning, flush, stream, seq_e2e, hbm_peak)
 
     cpu = None
@@ -1051,7 +1090,8 @@ def main():
         "gpu_launches": int(r["launches"]),
         "clocks": clocks.summary(),
         "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1], "march_blocks_per_sm": r["tuning"][2],
-                   "search_us": r["tune_entry"].get("us")},
+                   "px_tile": r["ext_tuning"][0], "col_shape": r["ext_tuning"][1],
+                   "search_us": r["tune_entry"].get("us"), "extract_search_us": r["ext_entry"].get("us")},
         other_wl: other,
         "batched": batched,
         "served": served,

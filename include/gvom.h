@@ -120,17 +120,28 @@ typedef struct gvom_maps_out {
 /* Largest scan gvom_ingest_scan accepts, in points. */
 #define GVOM_MAX_SCAN_POINTS ((int64_t)0x7fffffff)
 
-/* Launch shape of the ingest's traversal phase. A ray's in-window part is
- * cut into segments of at most seg_len voxel slabs along its major axis,
- * and a persistent grid of march_block-thread blocks (march_blocks_per_sm
- * per SM, 0 = as many as fit) walks them. Results do not depend on these;
- * speed does (the autotuner picks them per workload). Limits:
- * 1 <= seg_len <= 4096; march_block in {128, 256};
- * 0 <= march_blocks_per_sm <= 32; reserved = 0. */
+/* Launch shapes (results never depend on them; speed does, and the
+ * autotuner picks them per workload).
+ * Traversal: a ray's in-window part is cut into segments of at most
+ * seg_len voxel slabs along its major axis, and a persistent grid of
+ * march_block-thread blocks (march_blocks_per_sm per SM, 0 = as many as
+ * fit) walks them.
+ * Extraction of one map (gvom_extract_maps, gvom_update_extract):
+ * px_tile is the edge of the pixel pass's tiles (0 = the built-in rule),
+ * col_shape the column pass's bulk-copy chunks: 0 = 32 columns x 2 stages,
+ * 1 = 16 x 4, 2 = 32 x 3, 3 = 64 x 2 (a shape that does not fit shared
+ * memory for the map's nz falls back to 0). The batched and allocation-free
+ * extractions keep their built-in shapes.
+ * Limits: 1 <= seg_len <= 4096; march_block in {128, 256};
+ * 0 <= march_blocks_per_sm <= 32; px_tile 0 or in [4, 64] with the tile and
+ * its halo (the larger of neg_max_px and slope_n / 2) fitting 200 KiB of
+ * shared memory; 0 <= col_shape <= 3; reserved = 0. */
 typedef struct gvom_tuning {
     int32_t seg_len;
     int32_t march_block;
     int32_t march_blocks_per_sm;
+    int32_t px_tile;
+    int32_t col_shape;
     int32_t reserved;
 } gvom_tuning;
 
@@ -159,7 +170,8 @@ GVOM_API void gvom_destroy(struct gvom_map* map);
 /* The configuration the map was created with. */
 GVOM_API int gvom_get_config(const struct gvom_map* map, gvom_config* out);
 
-/* Default tuning: seg_len 16, march_block 256, blocks per SM as fit. */
+/* Default tuning: seg_len 16, march_block 256, blocks per SM as fit,
+ * built-in pixel tiles, 32-column 2-stage column chunks. */
 GVOM_API int gvom_tuning_default(gvom_tuning* out);
 
 /* Sets / reads the map's tuning (see gvom_tuning). Takes effect from the

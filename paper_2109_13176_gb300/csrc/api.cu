@@ -83,6 +83,8 @@ ExtractParams extract_params(const gvom_map* m) {
     p.slope_min_px = m->cfg.slope_min_px;
     p.neg_max_px = m->cfg.neg_max_px;
     p.neg_thresh = m->cfg.neg_thresh;
+    p.px_tile = m->tune.px_tile;
+    p.col_shape = m->tune.col_shape;
     return p;
 }
 
@@ -100,7 +102,9 @@ bool valid_pose(const double T[12]) {
 
 bool valid_tuning(const gvom_tuning* t) {
     return t && t->seg_len >= 1 && t->seg_len <= 4096 && (t->march_block == 128 || t->march_block == 256) &&
-           t->march_blocks_per_sm >= 0 && t->march_blocks_per_sm <= 32 && t->reserved == 0;
+           t->march_blocks_per_sm >= 0 && t->march_blocks_per_sm <= 32 &&
+           (t->px_tile == 0 || (t->px_tile >= 4 && t->px_tile <= 64)) && t->col_shape >= 0 && t->col_shape <= 3 &&
+           t->reserved == 0;
 }
 
 // Grows the ray records and the segment work list to hold a scan of n points
@@ -156,12 +160,20 @@ int gvom_tuning_default(gvom_tuning* out) {
     out->seg_len = 16;
     out->march_block = 256;
     out->march_blocks_per_sm = 0;
+    out->px_tile = 0;
+    out->col_shape = 0;
     out->reserved = 0;
     return GVOM_OK;
 }
 
 int gvom_set_tuning(gvom_map* m, const gvom_tuning* t) {
     if (!m || !valid_tuning(t)) return GVOM_ERR_INVALID_ARG;
+    if (t->px_tile > 0) {
+        // the pixel pass's tile and halo must fit one block's shared memory
+        gvom_map probe = *m;
+        probe.tune = *t;
+        if (gvom::slope_negative_smem(extract_params(&probe)) > 200 * 1024) return GVOM_ERR_INVALID_ARG;
+    }
     m->tune = *t;
     return GVOM_OK;
 }

@@ -248,7 +248,10 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
             if (maps[j] == mp) return GVOM_ERR_INVALID_ARG;  // one update per map per step
         total += n[m];
         items += n[m] * gvom::max_segments_per_ray(gvom::geom_of(mp), b->tune.seg_len);
-        const size_t pm = gvom::slope_negative_smem(gvom::extract_params(mp));
+        gvom::ExtractParams pmp = gvom::extract_params(mp);
+        pmp.px_tile = 0;  // the batched passes use their own fixed shapes
+        pmp.col_shape = 0;
+        const size_t pm = gvom::slope_negative_smem(pmp);
         px_smem = pm > px_smem ? pm : px_smem;
         const int nz = mp->cfg.nz;
         if (zmax >= 0) zmax = ((nz & 3) == 0 && nz <= 256) ? (nz > zmax ? nz : zmax) : -1;
@@ -315,6 +318,8 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
         BatchExtract& ex = h.ex[m];
         ex.s = mp->s;
         ex.p = gvom::extract_params(mp);
+        ex.p.px_tile = 0;
+        ex.p.col_shape = 0;
         const gvom_maps_out* o = outs ? outs + m : nullptr;
         ex.height = (o && o->height_dev) ? o->height_dev : mp->height_scratch;
         ex.density = o ? o->density_dev : nullptr;

@@ -271,10 +271,25 @@ __global__ void __launch_bounds__(kColBlock) k_columns(MapState s, ExtractParams
 // 3 x 32 columns fit shared memory; each stage's transaction count stays
 // below the mbarrier's 2^20 bytes).
 
-constexpr int kTmaCols = 32;      // columns per chunk
+// Chunk shapes (columns per bulk-copy chunk x stages in flight): the default
+// 32 x 2 and the variants the tuner may pick (gvom_tuning.col_shape).
+constexpr int kTmaCols = 32;      // columns per chunk of the default shape (and of the batched form)
 constexpr int kTmaStages = 2;
 constexpr int kTmaBlock = 256;
-size_t columns_tma_smem(int nz) { return 128 + (size_t)kTmaStages * 3 * kTmaCols * nz * sizeof(float); }
+size_t columns_tma_smem(int nz, int cols = kTmaCols, int stages = kTmaStages) {
+    return 128 + (size_t)stages * 3 * cols * nz * sizeof(float);
+}
+struct ColShape {
+    int cols, stages;
+};
+__host__ __device__ __forceinline__ ColShape col_shape_of(int code) {
+    switch (code) {
+        case 1: return ColShape{16, 4};
+        case 2: return ColShape{32, 3};
+        case 3: return ColShape{64, 2};
+        default: return ColShape{32, 2};
+    }
+}
 
 // One chunk of kTmaCols consecutive physical columns of one map.
 struct ChunkRef {
@@ -286,7 +301,8 @@ struct ChunkRef {
     long long lc;  // the chunk's index within its map
 };
 
-// The chunks of one map.
+// The chunks of one map (kCols columns each).
+template <int kCols>
 struct OneMapChunks {
     MapState s;
     ExtractParams p;
@@ -294,7 +310,7 @@ struct OneMapChunks {
     float* density;
     uint8_t* flags;
     __device__ __forceinline__ long long total() const {
-        return ((long long)p.g.nx * p.g.ny + kTmaCols - 1) / kTmaCols;
+        return ((long long)p.g.nx * p.g.ny + kCols - 1) / kCols;
     }
     __device__ __forceinline__ ChunkRef at(long long c) const { return ChunkRef{s, p, height, density, flags, c}; }
 };
@@ -319,16 +335,17 @@ struct BatchChunks {
     }
 };
 
-// Starts the copies of chunk r into `stage` (stage buffers hold kTmaCols
+// Starts the copies of chunk r into `stage` (stage buffers hold kCols
 // columns of zmax voxels; the chunk's own columns are nz long).
+template <int kCols>
 __device__ __forceinline__ void tma_issue(const ChunkRef& r, int zmax, int stage, unsigned long long* bars, uint32_t* hb,
                                           float* mb, uint32_t* pb) {
     const int nz = r.p.g.nz;
     const long long ncols = (long long)r.p.g.nx * r.p.g.ny;
-    const long long c0 = r.lc * kTmaCols;
-    const long long cols = ncols - c0 < kTmaCols ? ncols - c0 : kTmaCols;
+    const long long c0 = r.lc * kCols;
+    const long long cols = ncols - c0 < kCols ? ncols - c0 : kCols;
     const unsigned bytes = (unsigned)(cols * nz * 4);
-    const size_t so = (size_t)stage * kTmaCols * zmax;
+    const size_t so = (size_t)stage * kCols * zmax;
     if (!in_bounds((unsigned long long)(c0 + cols) * nz - 1, r.s.V, r.s.counters)) {
         mbar_arrive(&bars[stage]);  // nothing copied; the stage completes empty
         return;
@@ -342,36 +359,39 @@ __device__ __forceinline__ void tma_issue(const ChunkRef& r, int zmax, int stage
 // The bulk-copy column pass over the chunks of `src` (a persistent grid;
 // every map's nz is a multiple of 4 and at most zmax <= 256). A wait that
 // gives up sets the status word of the map whose chunk it waited for.
-template <typename Src>
+template <int kCols, int kStages, typename Src>
 __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
+    // kLanes lanes reduce one column: 256 threads cover the chunk's kCols columns
+    constexpr int kLanes = kTmaBlock / kCols;
+    static_assert(kLanes >= 4 && kLanes <= 32 && (kLanes & (kLanes - 1)) == 0, "lanes per column");
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ int s_fail;
     const long long nchunks = src.total();
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(sm);
     uint32_t* hb = reinterpret_cast<uint32_t*>(sm + 128);
-    float* mb = reinterpret_cast<float*>(hb + (size_t)kTmaStages * kTmaCols * zmax);
-    uint32_t* pb = reinterpret_cast<uint32_t*>(mb + (size_t)kTmaStages * kTmaCols * zmax);
+    float* mb = reinterpret_cast<float*>(hb + (size_t)kStages * kCols * zmax);
+    uint32_t* pb = reinterpret_cast<uint32_t*>(mb + (size_t)kStages * kCols * zmax);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int sub = lane & 7;                      // lane within the column's 8-lane group
+    const int sub = lane & (kLanes - 1);           // lane within the column's group
 
     if (tid == 0) {
-        for (int st = 0; st < kTmaStages; ++st) mbar_init(&bars[st], 1);
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (tid == 0)
-        for (int st = 0; st < kTmaStages; ++st) {
+        for (int st = 0; st < kStages; ++st) {
             const long long c = blockIdx.x + (long long)st * gridDim.x;
-            if (c < nchunks) tma_issue(src.at(c), zmax, st, bars, hb, mb, pb);
+            if (c < nchunks) tma_issue<kCols>(src.at(c), zmax, st, bars, hb, mb, pb);
         }
 
     int k = 0;
     for (;; ++k) {
         const long long c = blockIdx.x + (long long)k * gridDim.x;
         if (c >= nchunks) break;
-        const int st = k % kTmaStages;
-        if (!mbar_wait(&bars[st], (unsigned)((k / kTmaStages) & 1))) s_fail = 1;
+        const int st = k % kStages;
+        if (!mbar_wait(&bars[st], (unsigned)((k / kStages) & 1))) s_fail = 1;
         __syncthreads();
         if (s_fail) break;
         const ChunkRef r = src.at(c);
@@ -380,13 +400,13 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
         const int nz = g.nz, nv = nz >> 2;
         const long long ncols = (long long)g.nx * g.ny;
         const Band band = make_band(p.obs_min_h, p.obs_max_h);
-        const size_t so = (size_t)st * kTmaCols * zmax;
+        const size_t so = (size_t)st * kCols * zmax;
         const uint32_t* hst = hb + so;
         const float* mst = mb + so;
         const uint32_t* pst = pb + so;
-        const long long c0 = r.lc * kTmaCols;
-        // 8 warps x 4 columns = the chunk's 32 columns
-        const int j = warp * 4 + (lane >> 3);
+        const long long c0 = r.lc * kCols;
+        // 8 warps x (32 / kLanes) columns = the chunk's kCols columns
+        const int j = warp * (32 / kLanes) + lane / kLanes;
         const long long pc = c0 + j;                 // physical column
         const bool have = pc < ncols;
         const uint4* hv4 = reinterpret_cast<const uint4*>(hst + (size_t)j * nz);
@@ -394,7 +414,7 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
         float h = __int_as_float(0x7f800000);
         bool any = false;
         if (have)
-            for (int v = sub; v < nv; v += 8) {
+            for (int v = sub; v < nv; v += kLanes) {
                 const uint4 a = hv4[v];
                 const float4 b = mv4[v];
                 if (a.x) { h = fminf(h, b.x); any = true; }
@@ -403,13 +423,13 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
                 if (a.w) { h = fminf(h, b.w); any = true; }
             }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
-        const unsigned gm = 0xffu << (lane & 24);
+        for (int o = kLanes / 2; o > 0; o >>= 1) h = fminf(h, __shfl_xor_sync(0xffffffffu, h, o));
+        const unsigned gm = kLanes == 32 ? 0xffffffffu : (((1u << kLanes) - 1u) << (lane & ~(kLanes - 1)));
         const bool col_any = (__ballot_sync(0xffffffffu, any) & gm) != 0u;
         unsigned long long H = 0, M = 0;
         bool inband = false;
         if (have && col_any)
-            for (int v = sub; v < nv; v += 8) {
+            for (int v = sub; v < nv; v += kLanes) {
                 const uint4 a = hv4[v];
                 const float4 b = mv4[v];
                 const uint4 pm = reinterpret_cast<const uint4*>(pst + (size_t)j * nz)[v];
@@ -426,7 +446,7 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
             }
         if (__ballot_sync(0xffffffffu, inband)) {
 #pragma unroll
-            for (int o = 4; o > 0; o >>= 1) {
+            for (int o = kLanes / 2; o > 0; o >>= 1) {
                 H += __shfl_xor_sync(0xffffffffu, H, o);
                 M += __shfl_xor_sync(0xffffffffu, M, o);
             }
@@ -452,31 +472,32 @@ __device__ __forceinline__ void columns_tma_body(const Src& src, int zmax) {
         }
         __syncthreads();  // every warp is done with this stage
         if (tid == 0) {
-            const long long c2 = c + (long long)kTmaStages * gridDim.x;
-            if (c2 < nchunks) tma_issue(src.at(c2), zmax, st, bars, hb, mb, pb);
+            const long long c2 = c + (long long)kStages * gridDim.x;
+            if (c2 < nchunks) tma_issue<kCols>(src.at(c2), zmax, st, bars, hb, mb, pb);
         }
     }
     if (s_fail && tid == 0) {
         // drain the copies this block issued and has not consumed, then report
-        for (int q = k; q < k + kTmaStages; ++q) {
+        for (int q = k; q < k + kStages; ++q) {
             const long long c = blockIdx.x + (long long)q * gridDim.x;
             if (c >= nchunks) break;
-            mbar_wait(&bars[q % kTmaStages], (unsigned)((q / kTmaStages) & 1));
+            mbar_wait(&bars[q % kStages], (unsigned)((q / kStages) & 1));
         }
         atomicOr(src.at(blockIdx.x + (long long)k * gridDim.x).s.counters + kStatus, kStatusTimeout);
     }
 }
 
+template <int kCols, int kStages>
 __global__ void __launch_bounds__(kTmaBlock) k_columns_tma(MapState s, ExtractParams p, float* __restrict__ height,
                                                             float* __restrict__ density,
                                                             uint8_t* __restrict__ flags) {
     pdl_wait();
-    columns_tma_body(OneMapChunks{s, p, height, density, flags}, p.g.nz);
+    columns_tma_body<kCols, kStages>(OneMapChunks<kCols>{s, p, height, density, flags}, p.g.nz);
     pdl_done();
 }
 
 __global__ void __launch_bounds__(kTmaBlock) k_columns_tma_batch(BatchTables t, int zmax) {
-    columns_tma_body(BatchChunks{t}, zmax);
+    columns_tma_body<kTmaCols, kTmaStages>(BatchChunks{t}, zmax);
 }
 
 // Tile edge of the pixel pass for halo R: for R <= 12 the tile whose row
@@ -499,6 +520,7 @@ __host__ __device__ __forceinline__ int tile_for(int R, int nx, int ny) {
 }
 
 __host__ __device__ __forceinline__ int tile_edge(const ExtractParams& p) {
+    if (p.px_tile > 0) return p.px_tile;  // the tuner's choice
     const int R = p.neg_max_px > p.slope_n / 2 ? p.neg_max_px : p.slope_n / 2;
     return tile_for(R, p.g.nx, p.g.ny);
 }
@@ -893,20 +915,37 @@ cudaError_t launch_batch_extract(const BatchTables& t, int max_maps, size_t px_s
     return cudaGetLastError();
 }
 
+template <int kCols, int kStages>
+cudaError_t launch_columns_tma(const MapState& s, const ExtractParams& p, float* height, float* density,
+                               uint8_t* flags, long long cols, cudaStream_t st) {
+    const size_t smem = columns_tma_smem(p.g.nz, kCols, kStages);
+    static std::atomic<int> cache[64];
+    cudaError_t e = allow_smem((const void*)k_columns_tma<kCols, kStages>, cache, smem);
+    if (e != cudaSuccess) return e;
+    const long long chunks = (cols + kCols - 1) / kCols;
+    long long blocks = (long long)sm_count() * columns_tma_blocks_per_sm(smem);
+    if (blocks > chunks) blocks = chunks;
+    count_launch();
+    return launch_pdl(k_columns_tma<kCols, kStages>, dim3((unsigned)blocks), dim3(kTmaBlock), smem, st, s, p, height,
+                      density, flags);
+}
+
 cudaError_t launch_columns(const MapState& s, const ExtractParams& p, float* height, float* density, uint8_t* flags,
                            cudaStream_t st) {
     const long long cols = (long long)p.g.nx * p.g.ny;
     if ((p.g.nz & 3) == 0 && p.g.nz <= 256 && s.counters != nullptr) {
-        const size_t smem = columns_tma_smem(p.g.nz);
-        static std::atomic<int> cache[64];
-        cudaError_t e = allow_smem((const void*)k_columns_tma, cache, smem);
-        if (e != cudaSuccess) return e;
-        const long long chunks = (cols + kTmaCols - 1) / kTmaCols;
-        long long blocks = (long long)sm_count() * columns_tma_blocks_per_sm(smem);
-        if (blocks > chunks) blocks = chunks;
-        count_launch();
-        return launch_pdl(k_columns_tma, dim3((unsigned)blocks), dim3(kTmaBlock), smem, st, s, p, height, density,
-                          flags);
+        // a shape whose stages do not fit shared memory (or exceed a
+        // barrier's transaction count) falls back to the default one
+        ColShape cs = col_shape_of(p.col_shape);
+        if (columns_tma_smem(p.g.nz, cs.cols, cs.stages) > 200 * 1024 ||
+            (size_t)3 * cs.cols * p.g.nz * 4 >= (1u << 20))
+            cs = col_shape_of(0);
+        switch (cs.cols * 16 + cs.stages) {
+            case 16 * 16 + 4: return launch_columns_tma<16, 4>(s, p, height, density, flags, cols, st);
+            case 32 * 16 + 3: return launch_columns_tma<32, 3>(s, p, height, density, flags, cols, st);
+            case 64 * 16 + 2: return launch_columns_tma<64, 2>(s, p, height, density, flags, cols, st);
+            default: return launch_columns_tma<32, 2>(s, p, height, density, flags, cols, st);
+        }
     }
     count_launch();
     if ((p.g.nz & 3) != 0) {

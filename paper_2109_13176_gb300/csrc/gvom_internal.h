@@ -143,6 +143,8 @@ struct ExtractParams {
     int slope_n, slope_min_px;
     int neg_max_px;
     float neg_thresh;
+    int px_tile;    // pixel tile edge, 0: the built-in rule (gvom_tuning.px_tile)
+    int col_shape;  // column pass chunk shape code, 0: 32 columns x 2 stages (gvom_tuning.col_shape)
 };
 
 // ---- Batched update of many maps (tables filled by the host each step) ----

@@ -93,6 +93,8 @@ extern "C" int gvom_extract_maps_noalloc(const gvom_config* cfg, const uint32_t*
     p.slope_min_px = cfg->slope_min_px;
     p.neg_max_px = cfg->neg_max_px;
     p.neg_thresh = cfg->neg_thresh;
+    p.px_tile = 0;  // built-in shapes
+    p.col_shape = 0;
     gvom::MapState s = {};
     s.hits = const_cast<uint32_t*>(hits_dev);  // read only
     s.passes = const_cast<uint32_t*>(passes_dev);

@@ -1,8 +1,11 @@
-"""Autotuner for the traversal launch shape (gvom_tuning).
+"""Autotuner for the launch shapes (gvom_tuning).
 
 The segment walk's speed depends on the segment length (shorter segments
 balance warps better but cost more set-up) and on the block shape of its
 persistent grid; the best pair depends on the map, the sensor and the GPU.
+The extraction's speed depends on the pixel pass's tile edge (halo work
+against blocks in flight) and on the column pass's bulk-copy chunk shape
+(columns per chunk against stages in flight); tune_extract searches those.
 The tuner times each candidate on the caller's own workload, keeps the
 fastest, and remembers it in a JSON table (GVOM_TUNE_CACHE, default
 ~/.cache/gvom/tuning.json) under a key naming the device and the workload,
@@ -56,7 +59,7 @@ def search(run, candidates=CANDIDATES, repeats: int = 3):
         run(c)  # warm-up (first launch, scratch growth)
         times[c] = statistics.median(run(c) for _ in range(repeats))
     best = min(times, key=times.get)
-    return best, {f"{c[0]}/{c[1]}/{c[2]}": round(t * 1e6, 2) for c, t in times.items()}
+    return best, {"/".join(str(x) for x in c): round(t * 1e6, 2) for c, t in times.items()}
 
 
 def tuned(key: str, run, candidates=CANDIDATES, repeats: int = 3, refresh: bool = False):
@@ -96,6 +99,51 @@ def tune_map(vmap, scans_dev, poses, vehicles, flush=None, refresh: bool = False
     key = workload_key("map", vmap.shape, vmap.cfg.res, int(statistics.median(int(p.shape[0]) for p in scans_dev)))
     best, entry = tuned(key, run, repeats=repeats, refresh=refresh)
     vmap.set_tuning(*best)
+    return best, entry
+
+
+def extract_candidates(vmap):
+    """Pixel tile edges and column chunk shapes to try for one map: the
+    built-in rule and tiles whose rows with both halos are one, two or three
+    warps wide (plus 16), times the four chunk shapes."""
+    R = max(vmap.cfg.neg_max_px, vmap.cfg.slope_n // 2)
+    tiles = {0, 16}
+    for w in (32, 64, 96):
+        t = w - 2 * R
+        if 4 <= t <= 64:
+            tiles.add(t)
+    return [(t, c) for t in sorted(tiles) for c in (0, 1, 2, 3)]
+
+
+def tune_extract(vmap, outs, flush=None, refresh: bool = False, repeats: int = 3):
+    """Tunes one VoxelMap's extraction shapes (pixel tile edge, column chunk
+    shape) on its current state, with the caller's output buffers."""
+    import torch
+    from paper_2109_13176_gb300 import GvomError
+    stream = torch.cuda.current_stream()
+    cands = []
+    for c in extract_candidates(vmap):
+        try:
+            vmap.set_extract_tuning(*c)
+            cands.append(c)
+        except GvomError:
+            pass  # does not fit shared memory for this map
+
+    def run(c):
+        vmap.set_extract_tuning(*c)
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vmap.extract_maps(outs)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) * 1e-3
+
+    cfg = vmap.cfg
+    key = workload_key(f"extract-r{max(cfg.neg_max_px, cfg.slope_n // 2)}", vmap.shape, cfg.res, 0)
+    best, entry = tuned(key, run, candidates=cands, repeats=repeats, refresh=refresh)
+    vmap.set_extract_tuning(*best)
     return best, entry
 
 
