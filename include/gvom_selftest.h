@@ -37,6 +37,16 @@ GVOM_API int gvom_selftest_wait_timeout(struct gvom_map* map, uint32_t spin_limi
  * returns GVOM_ERR_INVALID_ARG. Stream-ordered. */
 GVOM_API int gvom_selftest_bounds(struct gvom_map* map, gvom_stream_t stream);
 
+/* Checks the per-point pass's integer-pipe conversions (float -> double,
+ * double -> int and double -> float, round to nearest, ties to even)
+ * against CUDA's own on the GPU: each of the n 64-bit patterns at bits_dev
+ * is taken as a double and its low word as a float; every disagreement adds
+ * 1 to *mismatches_dev (device uint64, the caller zeroes it). NaN inputs
+ * are skipped; the double -> int conversion is checked where the library
+ * uses it, |d| < 2^30. Stream-ordered. */
+GVOM_API int gvom_selftest_conversions(const uint64_t* bits_dev, int64_t n, uint64_t* mismatches_dev,
+                                       gvom_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

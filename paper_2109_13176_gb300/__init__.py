@@ -142,6 +142,7 @@ def load_library():
             "gvom_import_state": ([vp, o3, vp, vp, vp, vp], ctypes.c_int),
             "gvom_selftest_wait_timeout": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
             "gvom_selftest_bounds": ([vp, vp], ctypes.c_int),
+            "gvom_selftest_conversions": ([vp, i64, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -544,6 +545,13 @@ def gvom_selftest_wait_timeout(handle: int, spin_limit: int = 1000, stream=None)
     the next gvom_get_stats reports GVOM_ERR_TIMEOUT."""
     _check(load_library().gvom_selftest_wait_timeout(handle, int(spin_limit), _stream_handle(stream)),
            "gvom_selftest_wait_timeout")
+
+
+def gvom_selftest_conversions(bits, mismatches, stream=None) -> None:
+    """bits: device int64 tensor of bit patterns; mismatches: device int64
+    tensor of one element (zeroed by the caller); see include/gvom_selftest.h."""
+    _check(load_library().gvom_selftest_conversions(bits.data_ptr(), bits.numel(), mismatches.data_ptr(),
+                                                    _stream_handle(stream)), "gvom_selftest_conversions")
 
 
 def gvom_selftest_bounds(handle: int, stream=None) -> None:

@@ -17,7 +17,7 @@ LIB = os.path.join(BUILD, "libgvom.so")
 LIB_CHECKED = os.path.join(BUILD, "checked", "libgvom_checked.so")
 SOURCES = ["ingest.cu", "extract.cu", "export.cu", "api.cu", "batch.cu", "pipeline.cu", "microbench.cu", "noalloc.cu",
            "selftest.cu"]
-HEADERS = ["gvom_internal.h", "device_sync.cuh", os.path.join("..", "..", "include", "gvom.h"),
+HEADERS = ["gvom_internal.h", "device_sync.cuh", "exact_convert.cuh", os.path.join("..", "..", "include", "gvom.h"),
            os.path.join("..", "..", "include", "gvom_microbench.h"),
            os.path.join("..", "..", "include", "gvom_selftest.h")]
 

@@ -23,6 +23,7 @@
 // Counts are order-free sums, so the result is bit-identical to walking
 // every ray whole in one thread.
 #include "gvom_internal.h"
+#include "exact_convert.cuh"
 
 namespace gvom {
 
@@ -72,7 +73,7 @@ __device__ __forceinline__ double xform_row(const double* T, double px, double p
 __device__ __forceinline__ bool quantise(double w, double S, double neg_o256, int* q) {
     const double s = __fma_rn(w, S, neg_o256);
     if (((unsigned)__double2hiint(s) & 0x7fffffffu) >= 0x41d00000u) return false;
-    *q = (int)__double2ll_rn(s);
+    *q = d2i_rne(s);  // round half to even, on the integer pipe
     return true;
 }
 
@@ -190,14 +191,15 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
         const float r2max_f = (float)a.r2max;
         if (isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok &&
             in_range(fx, fy, fz, r2max_f * (1.0f - 9.5367432e-7f), r2max_f * (1.0f + 9.5367432e-7f), a.r2max)) {
-            const double px = fx, py = fy, pz = fz;
+            // exact widening and narrowing on the integer pipe (see exact_convert.cuh)
+            const double px = f2d_exact(fx), py = f2d_exact(fy), pz = f2d_exact(fz);
             {
                 const double wx = xform_row(a.T + 0, px, py, pz);
                 const double wy = xform_row(a.T + 4, px, py, pz);
                 const double wzd = xform_row(a.T + 8, px, py, pz);
                 valid = quantise(wx, a.S, a.neg_o256[0], &q[0]) && quantise(wy, a.S, a.neg_o256[1], &q[1]) &&
                         quantise(wzd, a.S, a.neg_o256[2], &q[2]);
-                wz = __double2float_rn(wzd);
+                wz = d2f_rne(wzd);
             }
         }
     }

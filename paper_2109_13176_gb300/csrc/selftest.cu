@@ -6,6 +6,7 @@
 // in the map's status word, which gvom_get_stats reports.
 #include "gvom_internal.h"
 #include "device_sync.cuh"
+#include "exact_convert.cuh"
 #include "../../include/gvom_selftest.h"
 
 namespace gvom {
@@ -29,10 +30,41 @@ __global__ void k_bounds_selftest(MapState s) {
     if (in_bounds(k, s.V, s.counters)) s.hits[k] = 0u;  // not reached in a checked build
 }
 
+// Each input bit pattern taken as a double d and (its low word) as a float
+// f: the library's integer-pipe conversions against CUDA's own, counting
+// mismatches (the integer conversion only where it is used, |d| < 2^30).
+__global__ void k_conversion_selftest(const unsigned long long* __restrict__ bits, long long n,
+                                      unsigned long long* __restrict__ mismatches) {
+    unsigned long long bad = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double d = __longlong_as_double((long long)bits[i]);
+        const float f = __uint_as_float((uint32_t)bits[i]);
+        if (!isnan(d)) {
+            if (fabs(d) < 1073741824.0 && d2i_rne(d) != (int)__double2ll_rn(d)) bad += 1;
+            if (__float_as_uint(d2f_rne(d)) != __float_as_uint(__double2float_rn(d))) bad += 1;
+        }
+        if (!isnan(f) &&
+            __double_as_longlong(f2d_exact(f)) != __double_as_longlong((double)f))
+            bad += 1;
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace
 }  // namespace gvom
 
 extern "C" {
+
+int gvom_selftest_conversions(const uint64_t* bits_dev, int64_t n, uint64_t* mismatches_dev, gvom_stream_t stream) {
+    if (!bits_dev || !mismatches_dev || n < 0) return GVOM_ERR_INVALID_ARG;
+    if (n == 0) return GVOM_OK;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    gvom::count_launch();
+    gvom::k_conversion_selftest<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+        (const unsigned long long*)bits_dev, n, (unsigned long long*)mismatches_dev);
+    return gvom::cuda_status(cudaGetLastError());
+}
 
 int gvom_checked_build(void) {
 #ifdef GVOM_CHECKED

@@ -176,3 +176,35 @@ def test_checkpoint_restore_continues_like_the_original(gv):
                                                None) == gv.GVOM_ERR_INVALID_ARG
     for m in (a, b, c):
         m.close()
+
+
+def test_integer_pipe_conversions_match_cuda(gv):
+    # the per-point pass's float -> double, double -> int and double -> float
+    # conversions (bit-field arithmetic, round to nearest, ties to even)
+    # against CUDA's own conversions: random bit patterns and the edges
+    rng = np.random.default_rng(2109)
+    parts = [rng.integers(0, 2 ** 63, size=200_000, dtype=np.int64),
+             -rng.integers(0, 2 ** 63, size=200_000, dtype=np.int64)]
+    # ties and near-ties of the integer rounding: k + 0.5, k + 0.5 +- 1 ulp, |k| < 2^30
+    k = rng.integers(-(2 ** 30) + 2, 2 ** 30 - 2, size=50_000).astype(np.float64)
+    for v in (k + 0.5, np.nextafter(k + 0.5, np.inf), np.nextafter(k + 0.5, -np.inf), k, -k - 0.5,
+              np.array([0.5, -0.5, 1.5, -1.5, 2.5, 0.49999999999999994, -0.0, 0.0, 2 ** 30 - 0.5,
+                        -(2 ** 30) + 0.5])):
+        parts.append(np.asarray(v, dtype=np.float64).view(np.int64))
+    # ties of the float rounding: a float plus half its ulp, and neighbours
+    f = rng.uniform(-1e6, 1e6, size=50_000).astype(np.float32)
+    f64 = f.astype(np.float64)
+    ulp = np.abs(np.nextafter(f, np.float32(np.inf)).astype(np.float64) - f64)
+    for v in (f64 + ulp / 2, np.nextafter(f64 + ulp / 2, np.inf), np.nextafter(f64 + ulp / 2, -np.inf)):
+        parts.append(v.view(np.int64))
+    # extremes of the float range and subnormals, as doubles and as floats
+    ext = np.array([3.4028234663852886e38, 3.4028235677973366e38, 3.4028236e38, 1.1754943508222875e-38,
+                    1.1754942e-38, 1e-45, 7e-46, 1e-300, 1e300, 65504.0, 1.0, -1.0], dtype=np.float64)
+    parts.append(ext.view(np.int64))
+    fl = np.array([1e-45, 1e-40, 1.1754942e-38, 1.1754944e-38, 3.4e38, -0.0, 0.0, 1.0], dtype=np.float32)
+    parts.append(fl.view(np.uint32).astype(np.int64))
+    bits = torch.from_numpy(np.concatenate(parts)).cuda()
+    bad = torch.zeros(1, dtype=torch.int64, device="cuda")
+    gv.gvom_selftest_conversions(bits, bad)
+    torch.cuda.synchronize()
+    assert int(bad.item()) == 0
