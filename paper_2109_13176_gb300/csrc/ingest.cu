@@ -857,8 +857,8 @@ __global__ void k_init_state(uint32_t* __restrict__ hits, uint32_t* __restrict__
 // (|d_k| < n_k on every axis); g is the new window. The entering voxels are
 // the union of an x slab (|dx| whole columns deep), a y slab (the remaining
 // columns, |dy| deep) and a z slab (|dz| voxels of every remaining column).
-// k_shift_columns clears whole columns, one warp each; k_shift_zslab clears
-// the z slab, one thread per column.
+// k_shift_columns clears them in one launch: whole columns one warp each,
+// the z slab one column per lane.
 __device__ __forceinline__ uint32_t column_base(const Geom& g, int cx, int cy) {
     int px = cx + g.rx;
     px -= (px >= g.nx) ? g.nx : 0;
@@ -880,42 +880,45 @@ __device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
     }
 }
 
-__global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, long long n_xslab, long long n_units) {
+// One launch for the whole shift: warp units [0, n_cols) clear entering
+// columns whole (the x slab, then the rest of the y slab), the units after
+// them clear the z slab, 32 columns per unit (one per lane).
+__global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, int dz, long long n_xslab, long long n_cols,
+                                long long n_units) {
     pdl_wait();
     const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (u >= n_units) return;
     const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
-    int cx, cy;
-    if (u < n_xslab) {
-        const int k = (int)((unsigned)u / (unsigned)g.ny);
-        cx = dx > 0 ? g.nx - dx + k : k;
-        cy = (int)((unsigned)u % (unsigned)g.ny);
+    if (u < n_cols) {
+        int cx, cy;
+        if (u < n_xslab) {
+            const int k = (int)((unsigned)u / (unsigned)g.ny);
+            cx = dx > 0 ? g.nx - dx + k : k;
+            cy = (int)((unsigned)u % (unsigned)g.ny);
+        } else {
+            const long long w = u - n_xslab;
+            const int k = (int)((unsigned)w / (unsigned)ady), l = (int)((unsigned)w % (unsigned)ady);
+            cx = (dx > 0 ? 0 : adx) + k;
+            cy = dy > 0 ? g.ny - dy + l : l;
+        }
+        const uint32_t base = column_base(g, cx, cy);
+        for (int cz = lane; cz < g.nz; cz += 32) clear_voxel(s, base + (uint32_t)cz);
     } else {
-        const long long w = u - n_xslab;
-        const int k = (int)((unsigned)w / (unsigned)ady), l = (int)((unsigned)w % (unsigned)ady);
-        cx = (dx > 0 ? 0 : adx) + k;
-        cy = dy > 0 ? g.ny - dy + l : l;
-    }
-    const uint32_t base = column_base(g, cx, cy);
-    for (int cz = lane; cz < g.nz; cz += 32) clear_voxel(s, base + (uint32_t)cz);
-    pdl_done();
-}
-
-__global__ void k_shift_zslab(MapState s, Geom g, int dx, int dy, int dz) {
-    pdl_wait();
-    const int adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
-    const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int wy = g.ny - ady;
-    if (w >= (long long)(g.nx - adx) * wy) return;
-    const int cx = (dx > 0 ? 0 : adx) + (int)((unsigned)w / (unsigned)wy);
-    const int cy = (dy > 0 ? 0 : ady) + (int)((unsigned)w % (unsigned)wy);
-    const uint32_t base = column_base(g, cx, cy);
-    const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
-    for (int cz = z0; cz < z1; ++cz) {
-        int pz = cz + g.rz;
-        pz -= (pz >= g.nz) ? g.nz : 0;
-        clear_voxel(s, base + (uint32_t)pz);
+        // the z slab of the columns that stay: one column per lane
+        const int wy = g.ny - ady;
+        const long long w = (u - n_cols) * 32 + lane;
+        if (w < (long long)(g.nx - adx) * wy) {
+            const int cx = (dx > 0 ? 0 : adx) + (int)((unsigned)w / (unsigned)wy);
+            const int cy = (dy > 0 ? 0 : ady) + (int)((unsigned)w % (unsigned)wy);
+            const uint32_t base = column_base(g, cx, cy);
+            const int z0 = dz > 0 ? g.nz - dz : 0, z1 = dz > 0 ? g.nz : -dz;
+            for (int cz = z0; cz < z1; ++cz) {
+                int pz = cz + g.rz;
+                pz -= (pz >= g.nz) ? g.nz : 0;
+                clear_voxel(s, base + (uint32_t)pz);
+            }
+        }
     }
     pdl_done();
 }
@@ -1146,27 +1149,17 @@ cudaError_t launch_evict(const MapState& s, unsigned long long mask, cudaStream_
 
 cudaError_t launch_shift(const MapState& s, const Geom& g_new, const long long d[3], cudaStream_t st) {
     const int dx = (int)d[0], dy = (int)d[1], dz = (int)d[2];
-    const long long adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy, adz = dz < 0 ? -dz : dz;
+    const long long adx = dx < 0 ? -dx : dx, ady = dy < 0 ? -dy : dy;
     const long long n_xslab = adx * g_new.ny;
     const long long n_cols = n_xslab + (g_new.nx - adx) * ady;
-    if (n_cols > 0) {
-        const int block = 256;
-        const long long blocks = (n_cols * 32 + block - 1) / block;
-        count_launch();
-        const cudaError_t e =
-            launch_pdl(k_shift_columns, dim3((unsigned)blocks), dim3(block), 0, st, s, g_new, dx, dy, n_xslab, n_cols);
-        if (e != cudaSuccess) return e;
-    }
-    if (adz > 0) {
-        const long long n = (g_new.nx - adx) * (g_new.ny - ady);
-        if (n > 0) {
-            const int block = 256;
-            count_launch();
-            return launch_pdl(k_shift_zslab, dim3((unsigned)((n + block - 1) / block)), dim3(block), 0, st, s, g_new,
-                              dx, dy, dz);
-        }
-    }
-    return cudaSuccess;
+    const long long n_z = dz != 0 ? ((g_new.nx - adx) * (g_new.ny - ady) + 31) / 32 : 0;
+    const long long n_units = n_cols + n_z;
+    if (n_units == 0) return cudaSuccess;
+    const int block = 256;
+    const long long blocks = (n_units * 32 + block - 1) / block;
+    count_launch();
+    return launch_pdl(k_shift_columns, dim3((unsigned)blocks), dim3(block), 0, st, s, g_new, dx, dy, dz, n_xslab,
+                      n_cols, n_units);
 }
 
 template <bool kSlot, bool kPow2>
