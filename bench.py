@@ -133,6 +133,42 @@ def metric_of(workload: str) -> str:
     return METRIC if workload == "high_speed" else METRIC_SEQUENCE
 
 
+def config_of(workload: str, cfg, n_scans: int, world: int) -> dict:
+    """The workload as both arms name it (identical dicts)."""
+    ms = cfg.map
+    return {"workload": workload_text(workload, n_scans), "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
+            "points_per_scan": cfg.lidar.n, "scans": n_scans, "l2": L2_NOTE,
+            "parallelism": f"replicas x{world} (one map per GPU)"}
+
+
+def summary_of(line: dict) -> dict:
+    """The headline figures of every leg in a few hundred characters, last
+    in the line (so that a reader keeping only the line's tail still sees
+    them)."""
+    out = {"value_M": round(line["value"] / 1e6, 1), "e2e_M": round(line["e2e"]["value"] / 1e6, 1),
+           "walk_frac_coalesced": round(line["roofline"]["frac"], 3),
+           "walk_us": round(line["roofline"]["launch_us"], 1)}
+    other = line.get("sequence") or line.get("high_speed")
+    if other:
+        out["other_M"] = round(other["value"] / 1e6, 1)
+        out["other_e2e_M"] = round(other["e2e"]["value"] / 1e6, 1)
+    b = line.get("batched")
+    if b:
+        out["batched"] = {"M": round(b["rays_per_s_batched"] / 1e6, 1), "plain_M": round(b["rays_per_s_plain"] / 1e6, 1),
+                          "speedup": round(b["speedup"], 3), "ms": round(b["ms_per_step_batched"], 3),
+                          "graph_fixed_us": round(b["graph_fixed_cost"]["empty_step_us_median"], 1)}
+    v = line.get("served")
+    if v:
+        out["served"] = {"p50_ms": round(v["realtime"]["p50_ms"], 2), "p99_ms": round(v["realtime"]["p99_ms"], 2),
+                         "max_load_p99_lt_100ms": v["max_load_with_p99_under_100ms"],
+                         "sweep_p99_ms": {str(p["load"]): round(p["p99_ms"], 1) for p in v["load_sweep"]},
+                         "saturated_M": round(v["saturated"]["rays_per_s"] / 1e6, 1)}
+    n = line.get("next_rows")
+    if n:
+        out["pipeline_M"] = round(n["pipeline_e2e"]["value"] / 1e6, 1)
+    return out
+
+
 BATCHED_WORKLOAD = ("batched: {m} independent maps 256x256x64 @ 0.2 m, each its own terrain and trajectory, "
                     "scan sizes log-uniform in [8,192, 262,144] (subsets of a 128x2048 scan), 2 generated steps cycled")
 
@@ -397,9 +433,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded procedural terrain and lidar model)",
-            "config": {"workload": workload_text(args.workload, args.high_speed_scans),
-                       "map": [cfg.map.nx, cfg.map.ny, cfg.map.nz], "res_m": cfg.map.res,
-                       "points_per_scan": cfg.lidar.n, "scans": len(scans)},
+            "config": config_of(args.workload, cfg, args.high_speed_scans if args.workload == "high_speed" else 20,
+                                args.gpus),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"{len(timed)} full scans of the workload (shift + ingest + extract each)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -867,6 +902,7 @@ def plain_summary(args, r, workload, red_peak, red_coalesced, hbm_peak, peak_kin
             "rays_per_step": r["rays"] / steps, "pass_visits_per_step": r["visits"] / steps,
             "hits_per_step": r["hits"] / steps, "shift_ms_mean": statistics.mean(r["shift_ms"]),
             "ingest_ms_mean": statistics.mean(r["ingest_ms"]), "extract_ms_mean": statistics.mean(r["extract_ms"]),
+            "per_point_pass_ms_mean": statistics.mean(r["rays_pass_ms"]), "walk_ms_mean": statistics.mean(r["walk_ms"]),
             "roofline": walk_roofline(r, steps, red_coalesced, red_peak, workload),
             "roofline_ingest": ingest_roofline(r, steps, red_peak, workload),
             "roofline_step": roofline_step((r["visits"] + 2 * r["hits"]) / steps, red_peak, ms.nx * ms.ny * ms.nz, ms,
@@ -1069,17 +1105,15 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64 transform, int32 traversal, u32 counts, f32 maps",
         "data": f"synthetic (seeded procedural terrain, boxes, ditches; {cfg.lidar.beams}-beam lidar model)",
-        "config": {"workload": workload_text(main_wl, r["n_scans"]), "map": [ms.nx, ms.ny, ms.nz], "res_m": ms.res,
-                   "points_per_scan": cfg.lidar.n, "scans": r["n_scans"],
-                   "l2": L2_NOTE,
-                   "parallelism": f"replicas x{world} (one map per GPU)"},
+        "config": config_of(main_wl, cfg, r["n_scans"], world),
         "map_updates_per_s": steps * world / total_s,
         "rays_per_step": rays / (steps * world),
         "pass_visits_per_step": r["visits"] / steps,
         "step_ms": {"median": statistics.median(r["step_ms"]),
                     "p99": sorted(r["step_ms"])[int(0.99 * (len(r["step_ms"]) - 1))],
                     "shift_avg": statistics.mean(r["shift_ms"]), "ingest_avg": statistics.mean(r["ingest_ms"]),
-                    "extract_avg": statistics.mean(r["extract_ms"])},
+                    "extract_avg": statistics.mean(r["extract_ms"]),
+                    "per_point_pass_avg": statistics.mean(r["rays_pass_ms"]), "walk_avg": statistics.mean(r["walk_ms"])},
         "roofline": walk_roofline(r, steps, red_coalesced, red_peak, main_wl),
         "roofline_ingest": ingest_roofline(r, steps, red_peak, main_wl),
         "roofline_step": roofline_step(atom_per_launch, red_peak, ms.nx * ms.ny * ms.nz, ms, cfg.lidar.n, hbm_peak,
@@ -1097,6 +1131,7 @@ def main():
         "served": served,
         "next_rows": next_rows,
     }
+    line["summary"] = summary_of(line)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

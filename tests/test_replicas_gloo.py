@@ -88,4 +88,7 @@ def test_reference_arm_json_line(capsys, monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["map"] == [512, 512, 64]
+    # the same config dict as the GPU arm's line on this workload
+    import synth
+    assert line["config"] == bench.config_of("high_speed", synth.sequence_config("high_speed"), 40, 1)
     assert line["cpu_baseline"]["host"]["nproc"] >= 1 and line["cpu_baseline"]["host"]["model"]
