@@ -233,12 +233,17 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
     // each warp's segments out segment-major (all first segments of the
     // warp's rays, then all second segments, ...), so that the lanes that
     // later walk neighbouring items walk neighbouring rays at similar range.
+    // Every segment but a ray's last spans seg_len major slabs; the last ones
+    // (the ray's end or its exit from the window) vary, so they follow the
+    // full ones as one group: a warp of the walk then holds segments of
+    // similar length, and fewer of its lanes wait for the longest.
     __shared__ unsigned int warp_tot[kRaysBlock / 32];
     __shared__ unsigned long long block_base;
     unsigned int tot = (unsigned int)nseg;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)nseg);
+    const int nfull = nseg > 0 ? nseg - 1 : 0;  // this ray's full-length segments
+    const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)nfull);
     if (lane == 0) warp_tot[warp] = tot;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -251,11 +256,21 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
     for (int w = 0; w < warp; ++w) off += warp_tot[w];
     const unsigned int lt = (1u << lane) - 1u;
     for (int j = 0; j < wmax; ++j) {
-        const unsigned int m = __ballot_sync(0xffffffffu, nseg > j);
-        if (nseg > j) {
+        const unsigned int m = __ballot_sync(0xffffffffu, nfull > j);
+        if (nfull > j) {
             const unsigned long long slot = off + __popc(m & lt);
             if (slot < (unsigned long long)a.w.cap_items)
                 a.w.items[slot] = make_uint2((unsigned int)(ray_base + i), (unsigned int)j);
+        }
+        off += __popc(m);
+    }
+    {
+        // every ray's last segment
+        const unsigned int m = __ballot_sync(0xffffffffu, nseg > 0);
+        if (nseg > 0) {
+            const unsigned long long slot = off + __popc(m & lt);
+            if (slot < (unsigned long long)a.w.cap_items)
+                a.w.items[slot] = make_uint2((unsigned int)(ray_base + i), (unsigned int)(nseg - 1));
         }
         off += __popc(m);
     }
