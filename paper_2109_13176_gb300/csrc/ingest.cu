@@ -162,69 +162,81 @@ __device__ __forceinline__ bool ray_frame(const Geom& g, const int a[3], const i
     return f.khi >= f.klo;
 }
 
+// One point (index i < a.n): load, filter, FP64 transform and quantisation
+// to 1/256 voxel (Sec. III-C). True iff the ray is kept; then q holds the
+// endpoint and wz its height as a float.
+__device__ __forceinline__ bool point_ray(const IngestArgs& a, long long i, bool sensor_ok, int q[3], float& wz) {
+    const float* p = a.pts + i * a.stride;
+    float fx, fy, fz;
+    if (a.stride == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        fx = v.x;
+        fy = v.y;
+        fz = v.z;
+    } else {
+        fx = __ldg(p);
+        fy = __ldg(p + 1);
+        fz = __ldg(p + 2);
+    }
+    const float r2max_f = (float)a.r2max;
+    if (!(isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok &&
+          in_range(fx, fy, fz, r2max_f * (1.0f - 9.5367432e-7f), r2max_f * (1.0f + 9.5367432e-7f), a.r2max)))
+        return false;
+    // exact widening and narrowing on the integer pipe (see exact_convert.cuh)
+    const double px = f2d_exact(fx), py = f2d_exact(fy), pz = f2d_exact(fz);
+    const double wx = xform_row(a.T + 0, px, py, pz);
+    const double wy = xform_row(a.T + 4, px, py, pz);
+    const double wzd = xform_row(a.T + 8, px, py, pz);
+    const bool valid = quantise(wx, a.S, a.neg_o256[0], &q[0]) && quantise(wy, a.S, a.neg_o256[1], &q[1]) &&
+                       quantise(wzd, a.S, a.neg_o256[2], &q[2]);
+    wz = d2f_rne(wzd);
+    return valid;
+}
+
+// The endpoint voxel of a kept ray, if it is in the window: a hit and the
+// lowest return (Sec. III-A), in the map and in its ring slot. Returns 1 for
+// an in-window hit.
+__device__ __forceinline__ int apply_hit(const IngestArgs& a, const int q[3], float wz) {
+    const Geom& g = a.g;
+    const int ex = q[0] >> 8, ey = q[1] >> 8, ez = q[2] >> 8;
+    if (!in_window(g, ex, ey, ez)) return 0;
+    const uint32_t k = phys_index(g, ex, ey, ez);
+    if (in_bounds(k, a.s.V, a.s.counters)) {
+        atomicAdd(a.s.hits + k, 1u);
+        atomic_min_f32(a.s.minz + k, wz);
+    }
+    if (a.slot >= 0) {
+        const size_t o = (size_t)a.slot * a.s.V + k;
+        if (in_bounds(o, (unsigned long long)a.s.ring_K * a.s.V, a.s.counters)) {
+            atomicAdd(a.s.ring_hits + o, 1u);
+            atomic_min_f32(a.s.ring_minz + o, wz);
+        }
+    }
+    return 1;
+}
+
+// Traversal segments of a kept ray from sensor qo to endpoint q.
+__device__ __forceinline__ int segments_of(const IngestArgs& a, const int qo[3], const int q[3]) {
+    RayFrame f;
+    return ray_frame(a.g, qo, q, f) ? (f.khi - f.klo) / a.seg_len + 1 : 0;
+}
+
 // Phase 1: points -> hits, lowest returns, ray records and segment list.
 // Called by every thread of a block, for points i = first + threadIdx.x of
 // one map (map_id) whose ray records start at ray_base in the scratch.
 __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, const int qo[3], bool sensor_ok,
                                           long long ray_base, unsigned int map_id) {
     const long long i = first + threadIdx.x;
-    const Geom g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    bool valid = false;
     int q[3] = {0, 0, 0};
     float wz = 0.0f;
-
-    if (i < a.n) {
-        const float* p = a.pts + i * a.stride;
-        float fx, fy, fz;
-        if (a.stride == 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-            fx = v.x;
-            fy = v.y;
-            fz = v.z;
-        } else {
-            fx = __ldg(p);
-            fy = __ldg(p + 1);
-            fz = __ldg(p + 2);
-        }
-        const float r2max_f = (float)a.r2max;
-        if (isfinite(fx) && isfinite(fy) && isfinite(fz) && sensor_ok &&
-            in_range(fx, fy, fz, r2max_f * (1.0f - 9.5367432e-7f), r2max_f * (1.0f + 9.5367432e-7f), a.r2max)) {
-            // exact widening and narrowing on the integer pipe (see exact_convert.cuh)
-            const double px = f2d_exact(fx), py = f2d_exact(fy), pz = f2d_exact(fz);
-            {
-                const double wx = xform_row(a.T + 0, px, py, pz);
-                const double wy = xform_row(a.T + 4, px, py, pz);
-                const double wzd = xform_row(a.T + 8, px, py, pz);
-                valid = quantise(wx, a.S, a.neg_o256[0], &q[0]) && quantise(wy, a.S, a.neg_o256[1], &q[1]) &&
-                        quantise(wzd, a.S, a.neg_o256[2], &q[2]);
-                wz = d2f_rne(wzd);
-            }
-        }
-    }
-
+    const bool valid = i < a.n && point_ray(a, i, sensor_ok, q, wz);
     int hit_in_window = 0;
     int nseg = 0;
     if (valid) {
-        const int ex = q[0] >> 8, ey = q[1] >> 8, ez = q[2] >> 8;
-        if (in_window(g, ex, ey, ez)) {
-            const uint32_t k = phys_index(g, ex, ey, ez);
-            if (in_bounds(k, a.s.V, a.s.counters)) {
-                atomicAdd(a.s.hits + k, 1u);
-                atomic_min_f32(a.s.minz + k, wz);
-            }
-            if (a.slot >= 0) {
-                const size_t o = (size_t)a.slot * a.s.V + k;
-                if (in_bounds(o, (unsigned long long)a.s.ring_K * a.s.V, a.s.counters)) {
-                    atomicAdd(a.s.ring_hits + o, 1u);
-                    atomic_min_f32(a.s.ring_minz + o, wz);
-                }
-            }
-            hit_in_window = 1;
-        }
-        RayFrame f;
-        if (ray_frame(g, qo, q, f)) nseg = (f.khi - f.klo) / a.seg_len + 1;
+        hit_in_window = apply_hit(a, q, wz);
+        nseg = segments_of(a, qo, q);
     }
     if (i < a.n && in_bounds(ray_base + i, a.w.cap_points, a.s.counters))
         a.w.rays[ray_base + i] = make_int4(q[0], q[1], q[2], (int)((map_id << 16) | (unsigned)nseg));
@@ -627,6 +639,69 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
     visits = 0;
 }
 
+// Walks one segment per lane from its first in-window voxel until its
+// crossing budget runs out (live: the lane holds a segment), adding the pass
+// increments; returns the number of voxels this lane visited. All lanes of
+// the warp call it.
+template <bool kBatch, bool kSlot, bool kPow2>
+__device__ __forceinline__ unsigned int walk_run(Walk& w, bool live, int lane, uint32_t* passes, uint32_t* spasses,
+                                                 uint32_t vmap, unsigned long long* cnts) {
+    // Visit the current voxel (in the window by construction), then take
+    // the next crossing group; the segment's crossing budget ends the walk.
+    // The step is branch-free: a lane that stops keeps stepping its
+    // (no longer read) state until the whole warp has stopped.
+    unsigned int item_n = 0;
+    while (__any_sync(0xffffffffu, live)) {
+        // The voxel is in the window by construction. On power-of-two
+        // windows the masked index cannot leave the map anyway; on others
+        // the index is only formed for a voxel inside the window, so no
+        // access can leave the state arrays whatever the walk computes.
+        const bool visit = kPow2 ? live
+                                 : live && (unsigned)w.cM < (unsigned)w.nM && (unsigned)w.cA < (unsigned)w.nA &&
+                                       (unsigned)w.cB < (unsigned)w.nB;
+        const uint32_t key = visit ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
+        // runs of neighbouring lanes in the same voxel merge their
+        // increments: the run's first lane adds the run's length
+        bool boundary;
+        if (kBatch) {
+            const unsigned long long kk =
+                visit ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
+            const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
+            boundary = lane == 0 || prev != kk;
+        } else {
+            const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);  // every lane
+            boundary = lane == 0 || prev != key;
+        }
+        const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
+        if (visit && boundary && in_bounds(key, vmap, cnts)) {
+            const unsigned int after = starts & ~((2u << lane) - 1u);
+            const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
+            atomicAdd(passes + key, run);
+            if (kSlot && spasses) atomicAdd(spasses + key, run);
+        }
+        item_n += visit ? 1u : 0u;
+        const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
+        const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
+        const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
+        const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
+        if (kPow2) {
+            w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
+                    ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
+                    ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
+        } else {
+            w.cM = imad_s32(iM, w.dirM, w.cM);
+            w.cA = imad_s32(iA, w.dirA, w.cA);
+            w.cB = imad_s32(iB, w.dirB, w.cB);
+        }
+        w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
+        w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
+        w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
+        w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
+        live = live && w.rem > 0;
+    }
+    return item_n;
+}
+
 // kPow2: every window of the launch has power-of-two extents (the index of
 // the current voxel is stepped, not recomputed).
 // Resident blocks per SM the walk is compiled for (registers per thread
@@ -686,59 +761,7 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
                 live = walk_init(a1, qo1, b, (int)it.y, w);
             }
         }
-        // Visit the current voxel (in the window by construction), then take
-        // the next crossing group; the segment's crossing budget ends the walk.
-        // The step is branch-free: a lane that stops keeps stepping its
-        // (no longer read) state until the whole warp has stopped.
-        unsigned int item_n = 0;
-        while (__any_sync(0xffffffffu, live)) {
-            // The voxel is in the window by construction. On power-of-two
-            // windows the masked index cannot leave the map anyway; on others
-            // the index is only formed for a voxel inside the window, so no
-            // access can leave the state arrays whatever the walk computes.
-            const bool visit = kPow2 ? live
-                                     : live && (unsigned)w.cM < (unsigned)w.nM && (unsigned)w.cA < (unsigned)w.nA &&
-                                           (unsigned)w.cB < (unsigned)w.nB;
-            const uint32_t key = visit ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
-            // runs of neighbouring lanes in the same voxel merge their
-            // increments: the run's first lane adds the run's length
-            bool boundary;
-            if (kBatch) {
-                const unsigned long long kk =
-                    visit ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
-                const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
-                boundary = lane == 0 || prev != kk;
-            } else {
-                const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);  // every lane
-                boundary = lane == 0 || prev != key;
-            }
-            const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-            if (visit && boundary && in_bounds(key, vmap, cnts)) {
-                const unsigned int after = starts & ~((2u << lane) - 1u);
-                const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
-                atomicAdd(passes + key, run);
-                if (kSlot && spasses) atomicAdd(spasses + key, run);
-            }
-            item_n += visit ? 1u : 0u;
-            const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
-            const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
-            const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
-            const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
-            if (kPow2) {
-                w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
-                        ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
-                        ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
-            } else {
-                w.cM = imad_s32(iM, w.dirM, w.cM);
-                w.cA = imad_s32(iA, w.dirA, w.cA);
-                w.cB = imad_s32(iB, w.dirB, w.cB);
-            }
-            w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
-            w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
-            w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
-            w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
-            live = live && w.rem > 0;
-        }
+        const unsigned int item_n = walk_run<kBatch, kSlot, kPow2>(w, live, lane, passes, spasses, vmap, cnts);
         item_visits = item_n;
         if (kBatch && __any_sync(0xffffffffu, own_item != own)) {
             flush_visits(a1, descs, own, visits);
