@@ -560,7 +560,7 @@ def run_next_rows(args, gv, torch, cfg, scans, tuning, flush, stream, serial_e2e
 
     # asynchronous pipeline: pinned host scan in, pinned host products out
     m = gv.VoxelMap(**kw)
-    m.set_tuning(*tuning)
+    tune.apply_walk(m, tuning)
     pipe = gv.Pipeline(m, max(int(p.shape[0]) for p in host_pts))
     houts = [pipe.alloc_host_outs() for _ in range(3)]
     t = 0
@@ -645,7 +645,7 @@ def run_next_rows(args, gv, torch, cfg, scans, tuning, flush, stream, serial_e2e
 
     # 10-scan buffer: the same step on a map that holds its last 10 scans
     mb = gv.VoxelMap(scan_buffer=10, **kw)
-    mb.set_tuning(*tuning)
+    tune.apply_walk(mb, tuning)
     ob = mb.alloc_maps()
 
     def buffered_step(k):
@@ -661,8 +661,8 @@ def run_next_rows(args, gv, torch, cfg, scans, tuning, flush, stream, serial_e2e
     # four sensors per scan (each scan cut into four quarters, one pose each)
     quarters = [[p[j * (p.shape[0] // 4):(j + 1) * (p.shape[0] // 4)] for j in range(4)] for p in dev_pts]
     mm, mseq = gv.VoxelMap(**kw), gv.VoxelMap(**kw)
-    mm.set_tuning(*tuning)
-    mseq.set_tuning(*tuning)
+    tune.apply_walk(mm, tuning)
+    tune.apply_walk(mseq, tuning)
 
     def multi_step(k):
         s = scans[k % ns]

@@ -132,17 +132,24 @@ typedef struct gvom_maps_out {
  * 1 = 16 x 4, 2 = 32 x 3, 3 = 64 x 2 (a shape that does not fit shared
  * memory for the map's nz falls back to 0). The batched and allocation-free
  * extractions keep their built-in shapes.
+ * Ingest of one map (gvom_ingest_scan): fused_ingest = 1 has one persistent
+ * cooperative kernel (a grid of resident blocks) both list and walk a scan's
+ * segments, its warps taking point tiles and 32-segment chunks of the list
+ * from shared counters; 0 runs the two kernels (list, then walk). The fused
+ * kernel serves maps without a scan buffer, with at most 4096 segments per
+ * ray, on streams that are not capturing a graph; other ingests use the two
+ * kernels whatever this field says.
  * Limits: 1 <= seg_len <= 4096; march_block in {128, 256};
  * 0 <= march_blocks_per_sm <= 32; px_tile 0 or in [4, 64] with the tile and
  * its halo (the larger of neg_max_px and slope_n / 2) fitting 200 KiB of
- * shared memory; 0 <= col_shape <= 3; reserved = 0. */
+ * shared memory; 0 <= col_shape <= 3; fused_ingest 0 or 1. */
 typedef struct gvom_tuning {
     int32_t seg_len;
     int32_t march_block;
     int32_t march_blocks_per_sm;
     int32_t px_tile;
     int32_t col_shape;
-    int32_t reserved;
+    int32_t fused_ingest;
 } gvom_tuning;
 
 /* Counters since gvom_create (or gvom_reset_stats). */
@@ -171,7 +178,7 @@ GVOM_API void gvom_destroy(struct gvom_map* map);
 GVOM_API int gvom_get_config(const struct gvom_map* map, gvom_config* out);
 
 /* Default tuning: seg_len 16, march_block 256, blocks per SM as fit,
- * built-in pixel tiles, 32-column 2-stage column chunks. */
+ * built-in pixel tiles, 32-column 2-stage column chunks, two-kernel ingest. */
 GVOM_API int gvom_tuning_default(gvom_tuning* out);
 
 /* Sets / reads the map's tuning (see gvom_tuning). Takes effect from the
@@ -180,7 +187,7 @@ GVOM_API int gvom_set_tuning(struct gvom_map* map, const gvom_tuning* tuning);
 GVOM_API int gvom_get_tuning(const struct gvom_map* map, gvom_tuning* out);
 
 /* Sizes the map's per-scan scratch (16 bytes per point for ray records
- * plus 8 bytes per traversal segment, at most ceil(max(nx,ny,nz)/seg_len)
+ * plus 16 bytes per traversal segment, at most ceil(max(nx,ny,nz)/seg_len)
  * segments per point) for scans of up to max_points points, so that no
  * later ingest has to grow it. Growing waits for `stream` and reallocates.
  * Call it before capturing ingests into a CUDA graph. */

@@ -61,7 +61,7 @@ class gvom_maps_out(ctypes.Structure):
 class gvom_tuning(ctypes.Structure):
     _fields_ = [("seg_len", ctypes.c_int32), ("march_block", ctypes.c_int32),
                 ("march_blocks_per_sm", ctypes.c_int32), ("px_tile", ctypes.c_int32),
-                ("col_shape", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("col_shape", ctypes.c_int32), ("fused_ingest", ctypes.c_int32)]
 
 
 class gvom_stats(ctypes.Structure):
@@ -609,19 +609,27 @@ class VoxelMap:
     def shift(self, new_origin, stream=None):
         gvom_shift(self.handle, new_origin, stream)
 
-    def set_tuning(self, seg_len=16, march_block=256, march_blocks_per_sm=0, px_tile=None, col_shape=None):
-        """Walk shape; px_tile / col_shape (extraction shapes) keep their
-        current values when not given."""
+    def set_tuning(self, seg_len=16, march_block=256, march_blocks_per_sm=0, px_tile=None, col_shape=None,
+                   fused_ingest=None):
+        """Walk shape; px_tile / col_shape (extraction shapes) and fused_ingest
+        (one kernel lists and walks) keep their current values when not given."""
         cur = gvom_get_tuning(self.handle)
         px = cur.px_tile if px_tile is None else px_tile
         cs = cur.col_shape if col_shape is None else col_shape
-        gvom_set_tuning(self.handle, gvom_tuning(seg_len, march_block, march_blocks_per_sm, px, cs, 0))
+        fu = cur.fused_ingest if fused_ingest is None else int(bool(fused_ingest))
+        gvom_set_tuning(self.handle, gvom_tuning(seg_len, march_block, march_blocks_per_sm, px, cs, fu))
 
     def set_extract_tuning(self, px_tile=0, col_shape=0):
         """Extraction shapes only (see gvom_tuning); the walk's stay."""
         cur = gvom_get_tuning(self.handle)
         gvom_set_tuning(self.handle, gvom_tuning(cur.seg_len, cur.march_block, cur.march_blocks_per_sm, px_tile,
-                                                 col_shape, 0))
+                                                 col_shape, cur.fused_ingest))
+
+    def set_fused_ingest(self, on=True):
+        """One persistent kernel lists and walks each scan (see gvom_tuning)."""
+        cur = gvom_get_tuning(self.handle)
+        gvom_set_tuning(self.handle, gvom_tuning(cur.seg_len, cur.march_block, cur.march_blocks_per_sm, cur.px_tile,
+                                                 cur.col_shape, int(bool(on))))
 
     def reserve(self, max_points, stream=None):
         gvom_reserve(self.handle, max_points, stream)

@@ -104,7 +104,7 @@ bool valid_tuning(const gvom_tuning* t) {
     return t && t->seg_len >= 1 && t->seg_len <= 4096 && (t->march_block == 128 || t->march_block == 256) &&
            t->march_blocks_per_sm >= 0 && t->march_blocks_per_sm <= 32 &&
            (t->px_tile == 0 || (t->px_tile >= 4 && t->px_tile <= 64)) && t->col_shape >= 0 && t->col_shape <= 3 &&
-           t->reserved == 0;
+           (t->fused_ingest == 0 || t->fused_ingest == 1);
 }
 
 // Grows the ray records and the segment work list to hold a scan of n points
@@ -137,7 +137,10 @@ int ensure_capacity(gvom_map* m, long long n, cudaStream_t st) {
     m->w.cap_points = 0;
     m->w.cap_items = 0;
     e = cudaMalloc(&m->w.rays, sizeof(int4) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc(&m->w.items, sizeof(uint2) * (size_t)(cap * per_ray));
+    // 16 bytes per entry (the fused ingest's int4 entries), all zero: no
+    // entry carries a fused scan's tag before that scan writes it
+    if (e == cudaSuccess) e = cudaMalloc(&m->w.items, sizeof(int4) * (size_t)(cap * per_ray));
+    if (e == cudaSuccess) e = cudaMemset(m->w.items, 0, sizeof(int4) * (size_t)(cap * per_ray));
     if (e != cudaSuccess) {
         cudaFree(m->w.rays);
         cudaFree(m->w.items);
@@ -162,7 +165,7 @@ int gvom_tuning_default(gvom_tuning* out) {
     out->march_blocks_per_sm = 0;
     out->px_tile = 0;
     out->col_shape = 0;
-    out->reserved = 0;
+    out->fused_ingest = 0;
     return GVOM_OK;
 }
 
@@ -225,8 +228,8 @@ int gvom_create(const gvom_config* cfg, gvom_map** out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->s.minz, sizeof(float) * (size_t)V);
     if (e == cudaSuccess) e = cudaMalloc(&m->s.counters, sizeof(unsigned long long) * gvom::kCounters);
     if (e == cudaSuccess) e = cudaMalloc(&m->height_scratch, sizeof(float) * (size_t)cfg->nx * cfg->ny);
-    if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(m->w.item_count, 0, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&m->w.item_count, gvom::kScratchWords * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(m->w.item_count, 0, gvom::kScratchWords * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&m->lut_counts, sizeof(unsigned int) * (size_t)gvom::lut_blocks(V));
     m->s.V = (uint32_t)V;
     const int K = cfg->scan_buffer;
@@ -301,7 +304,8 @@ int gvom_reset(gvom_map* m, const int64_t origin[3], gvom_stream_t stream) {
     m->buf_head = 0;
     m->buf_occupied = 0;
     // the work list starts empty again (after an error mid-scan it may not be)
-    const cudaError_t e = cudaMemsetAsync(m->w.item_count, 0, 2 * sizeof(unsigned long long), (cudaStream_t)stream);
+    const cudaError_t e =
+        cudaMemsetAsync(m->w.item_count, 0, gvom::kScratchWords * sizeof(unsigned long long), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_status(e);
     return cuda_status(gvom::launch_init_state(m->s, voxels(m), (cudaStream_t)stream));
 }
@@ -360,6 +364,28 @@ int gvom_ingest_scan(gvom_map* m, const float* pts_dev, int64_t n, int32_t strid
     gvom::MarchShape shape;
     shape.block = m->tune.march_block;
     shape.blocks_per_sm = m->tune.march_blocks_per_sm;
+    shape.fused = false;
+    if (m->tune.fused_ingest && slot < 0 &&
+        gvom::max_segments_per_ray(a.g, a.seg_len) <= gvom::kFusedMaxSegments) {
+        // a captured launch would replay one tag: capturing streams take the
+        // two kernels
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+            cudaGetLastError();
+            cs = cudaStreamCaptureStatusActive;
+        }
+        if (cs == cudaStreamCaptureStatusNone) {
+            if (m->fused_epoch + 1 >= gvom::kFusedEpochs) {
+                // the tags are about to repeat: no entry may keep an old one
+                const cudaError_t e = cudaMemsetAsync(m->w.items, 0, sizeof(int4) * (size_t)m->w.cap_items,
+                                                      (cudaStream_t)stream);
+                if (e != cudaSuccess) return cuda_status(e);
+                m->fused_epoch = 0;
+            }
+            a.epoch = ++m->fused_epoch;
+            shape.fused = true;
+        }
+    }
     m->scans += 1;
     m->points_in += n;
     return cuda_status(gvom::launch_ingest(a, shape, (cudaStream_t)stream, m->walk_marker));

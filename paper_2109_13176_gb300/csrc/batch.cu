@@ -182,7 +182,7 @@ int gvom_batch_create(int32_t max_maps, int64_t max_points, int32_t flags, gvom_
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_tables[1], b->L.bytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied[1], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&b->w.item_count, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->w.item_count, gvom::kScratchWords * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&b->w.rays, sizeof(int4) * (size_t)max_points);
     if (e == cudaSuccess) b->w.cap_points = max_points;
@@ -356,6 +356,7 @@ int gvom_batch_step(gvom_batch* b, struct gvom_map* const* maps, int32_t B, cons
     gvom::MarchShape shape;
     shape.block = b->tune.march_block;
     shape.blocks_per_sm = b->tune.march_blocks_per_sm;
+    shape.fused = false;
     const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
     const int do_extract = outs != nullptr;
 
@@ -486,6 +487,7 @@ int ingest_multi(gvom_map* mp, int k, const float* const* pts_dev, const int64_t
     MarchShape shape;
     shape.block = mp->tune.march_block;
     shape.blocks_per_sm = mp->tune.march_blocks_per_sm;
+    shape.fused = false;
     const long long max_ray_blocks = (b->max_points + 255) / 256 + b->max_maps;
     return cuda_status(launch_batch_update(tables_at(b->d_tables, b->L), b->max_maps, max_ray_blocks, shared, shape,
                                            evict != 0ull, buffered, pow2_window(g), st));

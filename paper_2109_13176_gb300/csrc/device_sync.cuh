@@ -2,7 +2,9 @@
 // self-test: initialisation, plain and transaction arrivals, 1D bulk copies
 // completing on a barrier, and a wait with an iteration limit (a wait that
 // gives up returns false; the caller records kStatusTimeout in the map's
-// status word and returns, so no kernel waits forever).
+// status word and returns, so no kernel waits forever). Also the GPU-scope
+// acquire loads and relaxed stores that the fused ingest's warps use to
+// hand list entries to one another through global memory.
 #pragma once
 
 #include <stdint.h>
@@ -45,6 +47,32 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         if (done) return true;
     }
     return false;
+}
+
+// GPU-scope loads and stores of words other blocks write or poll. A
+// producer writes its data, then __threadfence(), then the flag with
+// st_relaxed_gpu; a consumer that reads the flag with ld_acquire_gpu then
+// sees the data.
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 }  // namespace gvom

@@ -106,10 +106,24 @@ __device__ __forceinline__ bool in_bounds(unsigned long long i, unsigned long lo
 // segment work list, and its length.
 struct RayScratch {
     int4* rays;               // cap_points entries: (qx, qy, qz, nseg)
-    uint2* items;             // cap_items entries: (point index, segment index)
-    unsigned long long* item_count; // two words: the list's length, and blocks of the walk done with it
+    // cap_items entries: (point index, segment index) as uint2 for the
+    // two-kernel ingest; on plain maps 16 bytes per entry are allocated, and
+    // the fused ingest uses them as int4 (qx, qy, qz, epoch << 12 | segment)
+    uint2* items;
+    unsigned long long* item_count; // kScratchWords words (ScratchWord)
     long long cap_points;
     long long cap_items;
+};
+
+// Words of RayScratch::item_count. Two-kernel ingest: the list's length and
+// the walk's blocks done with it. Fused ingest, each word on a 128-byte line
+// of its own (its warps poll them while others add to them): list entries
+// reserved, point tiles listed, blocks done. Every kernel leaves its words at
+// zero when it ends.
+enum ScratchWord {
+    kListLen = 0, kListBlocksDone = 1,
+    kFReserved = 16, kFTilesDone = 32, kFBlocksDone = 48,
+    kScratchWords = 64
 };
 
 // Per-scan arguments of the ingest kernels (passed by value).
@@ -127,12 +141,19 @@ struct IngestArgs {
     RayScratch w;
     int slot;            // ring slot this scan also goes to, -1: none
     int cnt_owner;       // batch entry whose counters this entry's visits go to
+    unsigned int epoch;  // fused ingest: this scan's list tag, 1 .. kFusedEpochs - 1
 };
+
+// Fused ingest: list entries carry the scan's tag in their top 20 bits and
+// the segment index in the low 12 (so at most kFusedMaxSegments per ray).
+constexpr unsigned int kFusedEpochs = 1u << 20;
+constexpr long long kFusedMaxSegments = 1 << 12;
 
 // Launch shape of the segment walk (tunable).
 struct MarchShape {
     int block;                // threads per block
     int blocks_per_sm;        // 0: as many as fit
+    bool fused;               // one persistent kernel lists and walks (plain maps, no slot)
 };
 
 struct ExtractParams {
@@ -275,6 +296,7 @@ struct gvom_map {
     unsigned long long buf_occupied; // ring slots holding a scan
     gvom_tuning tune;
     cudaEvent_t walk_marker;         // gvom_set_walk_marker (null: none)
+    unsigned int fused_epoch;        // tag of the last fused ingest's list entries
     long long scans;
     long long points_in;
     int device;

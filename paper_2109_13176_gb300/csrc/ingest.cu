@@ -24,6 +24,7 @@
 // every ray whole in one thread.
 #include "gvom_internal.h"
 #include "exact_convert.cuh"
+#include "device_sync.cuh"
 
 namespace gvom {
 
@@ -261,7 +262,7 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
     if (threadIdx.x == 0) {
         unsigned int s = 0;
         for (int w = 0; w < kRaysBlock / 32; ++w) s += warp_tot[w];
-        block_base = s ? atomicAdd(a.w.item_count, (unsigned long long)s) : 0ull;
+        block_base = s ? atomicAdd(a.w.item_count + kListLen, (unsigned long long)s) : 0ull;
     }
     __syncthreads();
     unsigned long long off = block_base;
@@ -714,7 +715,7 @@ template <bool kBatch, bool kSlot, bool kPow2>
 __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const IngestArgs a1, const IngestArgs* __restrict__ descs, const int4* __restrict__ sensors) {
     pdl_wait();
     const int lane = threadIdx.x & 31;
-    const unsigned long long total_items = *a1.w.item_count;
+    const unsigned long long total_items = a1.w.item_count[kListLen];
     const long long n_items =
         (long long)(total_items < (unsigned long long)a1.w.cap_items ? total_items : a1.w.cap_items);
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -776,9 +777,187 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
         // the last block to finish empties the work list for the next scan
         // (every thread of every block read its length at the start)
         __syncthreads();
-        if (threadIdx.x == 0 && atomicAdd(a1.w.item_count + 1, 1ull) + 1 == gridDim.x) {
-            a1.w.item_count[0] = 0;
-            a1.w.item_count[1] = 0;
+        if (threadIdx.x == 0 && atomicAdd(a1.w.item_count + kListBlocksDone, 1ull) + 1 == gridDim.x) {
+            a1.w.item_count[kListLen] = 0;
+            a1.w.item_count[kListBlocksDone] = 0;
+        }
+    }
+}
+
+// Fused ingest (tuning fused_ingest = 1): one persistent kernel whose warps
+// first list segments and then walk them, so the walk starts on the first
+// listed segments while other warps still list, with no launch between.
+// Work is assigned statically, as in the two-kernel walk, so no warp claims
+// work through a shared counter: global warp g of W lists point tiles
+// g, g + W, ... (32 points each) and then walks the list's 32-entry chunks
+// g, g + W, .... Entries are int4 (qx, qy, qz, tag) with tag = epoch << 12 |
+// segment index; a lane polls its entry's tag, so an entry an earlier scan
+// left in the list is never taken for this scan's, and a chunk past the
+// list's end is recognised once every tile is listed (the listed-tiles count
+// equals the tile count; the reserved count is then final).
+//
+// Every wait ends: a warp walks only after listing all its tiles, so the
+// entries it waits for are written by warps that are listing and do not
+// wait. No grid-wide residency is needed for progress; the launch is
+// cooperative (at most the blocks that fit at once) all the same, and every
+// wait is bounded (kStatusTimeout).
+
+// Lists one 32-point tile (points tile * 32 + lane): hits and lowest
+// returns, then the tile's segments at entries reserved with one atomic,
+// written in two passes: the coordinates, a fence, then the tags that
+// publish them. The count of listed tiles goes up last.
+__device__ __forceinline__ void fused_list_tile(const IngestArgs& a, long long tile, const int qo[3], bool sensor_ok,
+                                                int lane, unsigned int& n_valid, unsigned int& n_hit) {
+    const long long i = tile * 32 + lane;
+    int q[3] = {0, 0, 0};
+    float wz = 0.0f;
+    const bool valid = i < a.n && point_ray(a, i, sensor_ok, q, wz);
+    int nseg = 0;
+    if (valid) {
+        n_valid += 1u;
+        n_hit += (unsigned int)apply_hit(a, q, wz);
+        nseg = segments_of(a, qo, q);
+    }
+    const unsigned int tot = __reduce_add_sync(0xffffffffu, (unsigned int)nseg);
+    const int nfull = nseg > 0 ? nseg - 1 : 0;  // this ray's full-length segments
+    const int wmax = (int)__reduce_max_sync(0xffffffffu, (unsigned int)nfull);
+    unsigned long long base = 0ull;
+    if (lane == 0 && tot) base = atomicAdd(a.w.item_count + kFReserved, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    int4* const items = reinterpret_cast<int4*>(a.w.items);
+    const unsigned long long cap = (unsigned long long)a.w.cap_items;
+    const unsigned int lt = (1u << lane) - 1u;
+    const unsigned int tag = a.epoch << 12;
+    for (int pass = 0; pass < 2; ++pass) {
+        unsigned long long off = base;
+        for (int j = 0; j <= wmax; ++j) {  // j == wmax: every ray's last segment
+            const bool last = j == wmax;
+            const bool mine = last ? nseg > 0 : nfull > j;
+            const unsigned int m = __ballot_sync(0xffffffffu, mine);
+            const unsigned long long slot = off + __popc(m & lt);
+            if (mine && slot < cap) {
+                if (pass == 0) {
+                    items[slot] = make_int4(q[0], q[1], q[2], 0);
+                } else {
+                    const unsigned int seg = last ? (unsigned int)(nseg - 1) : (unsigned int)j;
+                    st_relaxed_gpu(reinterpret_cast<uint32_t*>(items + slot) + 3, tag | seg);
+                }
+            }
+            off += __popc(m);
+        }
+        // the coordinates (and lane 0's reservation) before any tag, and
+        // before the count of listed tiles
+        if (pass == 0) __threadfence();
+    }
+    __syncwarp();
+    if (lane == 0) atomicAdd(a.w.item_count + kFTilesDone, 1ull);
+}
+
+// The list's state as one warp sees it: lane 0 reads the listed-tiles count
+// (acquire) and then the reserved count, and shares both. Once every tile is
+// listed the reserved count read after it is the list's final length.
+__device__ __forceinline__ void fused_list_state(const IngestArgs& a, long long ntiles, int lane, bool& final,
+                                                 unsigned long long& end) {
+    unsigned long long e = 0ull;
+    int f = 0;
+    if (lane == 0) {
+        f = ld_acquire_gpu(a.w.item_count + kFTilesDone) == (unsigned long long)ntiles;
+        e = ld_relaxed_gpu(a.w.item_count + kFReserved);
+    }
+    final = __shfl_sync(0xffffffffu, f, 0) != 0;
+    end = __shfl_sync(0xffffffffu, e, 0);
+    if ((unsigned long long)a.w.cap_items < end) end = (unsigned long long)a.w.cap_items;
+}
+
+template <bool kPow2>
+__global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_ingest_fused(const IngestArgs a) {
+    pdl_wait();
+    int qo[3];
+    const bool sensor_ok = block_sensor(a, qo);  // every thread, before the warps part
+    const int lane = threadIdx.x & 31;
+    const long long ntiles = (a.n + 31) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int4* const items = reinterpret_cast<const int4*>(a.w.items);
+
+    // 1. this warp's point tiles
+    unsigned int n_valid = 0, n_hit = 0;  // kept points, in-window hits of this lane's points
+    for (long long t = gw; t < ntiles; t += nwarps) fused_list_tile(a, t, qo, sensor_ok, lane, n_valid, n_hit);
+
+    // 2. this warp's chunks of the list
+    unsigned long long visits = 0;  // pass visits of this lane's walks
+    unsigned long long end = 0;     // entries known to be reserved (warp-uniform)
+    bool final = false;             // end is the list's final length (warp-uniform)
+    bool gave_up = false;
+    for (unsigned long long c = (unsigned long long)gw * 32;; c += (unsigned long long)nwarps * 32) {
+        // until the chunk starts inside the list, or the list is final
+        for (unsigned int idle = 0; !(c < end) && !final;) {
+            fused_list_state(a, ntiles, lane, final, end);
+            if (c < end || final) break;
+            if (++idle > kSpinLimit) {
+                gave_up = true;
+                break;
+            }
+            __nanosleep(idle < 8 ? 128u : 1024u);
+        }
+        if (gave_up || !(c < end)) break;  // past the final list's end
+        // this lane's entry: wait for its tag (it is written by a warp still
+        // listing), or learn that it is past the final list's end
+        const unsigned long long idx = c + lane;
+        bool have = false, entry = false;
+        int4 it = make_int4(0, 0, 0, 0);
+        for (unsigned int idle = 0;;) {
+            if (!have) {
+                if (final && idx >= end) {
+                    have = true;
+                } else if (idx < end) {
+                    const unsigned int t = ld_acquire_gpu(reinterpret_cast<const uint32_t*>(items + idx) + 3);
+                    if ((t >> 12) == a.epoch) {
+                        it = __ldcg(items + idx);
+                        it.w = (int)(t & 0xfffu);
+                        have = entry = true;
+                    }
+                }
+            }
+            if (__all_sync(0xffffffffu, have)) break;
+            if (++idle > kSpinLimit) {
+                gave_up = true;
+                break;
+            }
+            __nanosleep(64);
+            if ((idle & 7u) == 0u) fused_list_state(a, ntiles, lane, final, end);
+        }
+        if (gave_up) break;
+        Walk w;
+        bool live = false;
+        if (entry) {
+            const int b[3] = {it.x, it.y, it.z};
+            live = walk_init(a, qo, b, it.w, w);
+        }
+        visits += walk_run<false, false, kPow2>(w, live, lane, a.s.passes, nullptr, a.s.V, a.s.counters);
+    }
+    // a wait that ran out: recorded, and this warp's remaining chunks stay
+    // unwalked (no warp waits on a walking warp)
+    if (gave_up && lane == 0) atomicOr(a.s.counters + kStatus, kStatusTimeout);
+
+    pdl_done();
+    flush_visits(a, nullptr, 0u, visits);
+    const unsigned int tv = __reduce_add_sync(0xffffffffu, n_valid);
+    const unsigned int th = __reduce_add_sync(0xffffffffu, n_hit);
+    if (lane == 0) {
+        if (tv) atomicAdd(a.s.counters + kRaysValid, (unsigned long long)tv);
+        if (th) atomicAdd(a.s.counters + kHitsInWindow, (unsigned long long)th);
+    }
+    // the last block to finish leaves the list's words at zero for the next
+    // scan (every warp of every block is past its last use of them)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long* const ctr = a.w.item_count;
+        __threadfence();
+        if (atomicAdd(ctr + kFBlocksDone, 1ull) + 1 == gridDim.x) {
+            ctr[kFReserved] = 0;
+            ctr[kFTilesDone] = 0;
+            ctr[kFBlocksDone] = 0;
         }
     }
 }
@@ -985,8 +1164,8 @@ __global__ void __launch_bounds__(256) k_shift_batch(BatchTables t) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid == 0) {
         // the step's segment work list starts empty (all entries share it)
-        t.ing[0].w.item_count[0] = 0;
-        t.ing[0].w.item_count[1] = 0;
+        t.ing[0].w.item_count[kListLen] = 0;
+        t.ing[0].w.item_count[kListBlocksDone] = 0;
     }
     if (tid < B) {
         const IngestArgs& a = t.ing[tid];
@@ -1208,8 +1387,46 @@ cudaError_t launch_march_one(const IngestArgs& a, const MarchShape& shape, cudaS
                       0, st, a, none, no_sensors);
 }
 
+// The fused ingest as a cooperative launch: one block per resident slot
+// (march_blocks_per_sm, if set, caps the blocks per SM).
+template <bool kPow2>
+cudaError_t launch_fused(const IngestArgs& a, const MarchShape& shape, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    static std::atomic<int> cache[64][2];  // resident blocks per SM, per device and block size
+    const int b = shape.block == 256 ? 1 : 0;
+    int nb = dev >= 0 && dev < 64 ? cache[dev][b].load(std::memory_order_relaxed) : 0;
+    if (nb <= 0) {
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ingest_fused<kPow2>, shape.block, 0);
+        if (e != cudaSuccess) return e;
+        if (nb <= 0) return cudaErrorLaunchOutOfResources;
+        if (dev >= 0 && dev < 64) cache[dev][b].store(nb, std::memory_order_relaxed);
+    }
+    const int per_sm = shape.blocks_per_sm > 0 && shape.blocks_per_sm < nb ? shape.blocks_per_sm : nb;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(sms * per_sm));
+    cfg.blockDim = dim3((unsigned)shape.block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_ingest_fused<kPow2>, a);
+}
+
 cudaError_t launch_ingest(const IngestArgs& a, const MarchShape& shape, cudaStream_t st, cudaEvent_t marker) {
     if (a.n <= 0) return cudaSuccess;
+    if (shape.fused) {
+        // one kernel lists and walks; the marker precedes it
+        cudaError_t e = cudaSuccess;
+        if (marker && (e = cudaEventRecord(marker, st)) != cudaSuccess) return e;
+        count_launch();
+        return pow2_window(a.g) ? launch_fused<true>(a, shape, st) : launch_fused<false>(a, shape, st);
+    }
     // the work list is empty here: the previous scan's walk emptied it
     const long long blocks = (a.n + kRaysBlock - 1) / kRaysBlock;
     count_launch();

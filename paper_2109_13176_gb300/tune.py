@@ -1,8 +1,9 @@
 """Autotuner for the launch shapes (gvom_tuning).
 
 The segment walk's speed depends on the segment length (shorter segments
-balance warps better but cost more set-up) and on the block shape of its
-persistent grid; the best pair depends on the map, the sensor and the GPU.
+balance warps better but cost more set-up), on the block shape of its
+persistent grid and on whether one fused kernel both lists and walks the
+segments; the best choice depends on the map, the sensor and the GPU.
 The extraction's speed depends on the pixel pass's tile edge (halo work
 against blocks in flight) and on the column pass's bulk-copy chunk shape
 (columns per chunk against stages in flight); tune_extract searches those.
@@ -18,7 +19,10 @@ import os
 import statistics
 import time
 
-CANDIDATES = [(L, blk, 0) for L in (8, 12, 16, 24, 32, 48, 64) for blk in (128, 256)]
+# walk shapes (seg_len, march_block, march_blocks_per_sm) for batches, and
+# with fused_ingest for single maps
+WALK_CANDIDATES = [(L, blk, 0) for L in (8, 12, 16, 24, 32, 48, 64) for blk in (128, 256)]
+CANDIDATES = [c + (f,) for c in WALK_CANDIDATES for f in (0, 1)]
 
 
 def cache_path() -> str:
@@ -65,7 +69,7 @@ def search(run, candidates=CANDIDATES, repeats: int = 3):
 def tuned(key: str, run, candidates=CANDIDATES, repeats: int = 3, refresh: bool = False):
     """The cached best candidate for key, or a fresh search (then cached)."""
     table = _load()
-    if not refresh and key in table:
+    if not refresh and key in table and len(table[key]["best"]) == len(candidates[0]):
         c = table[key]["best"]
         return tuple(c), table[key]
     t0 = time.perf_counter()
@@ -82,7 +86,7 @@ def tune_map(vmap, scans_dev, poses, vehicles, flush=None, refresh: bool = False
     stream = torch.cuda.current_stream()
 
     def run(c):
-        vmap.set_tuning(*c)
+        apply_walk(vmap, c)
         tot = 0.0
         for pts, T, v in zip(scans_dev, poses, vehicles):
             vmap.shift(vmap.origin_for_pose(v))
@@ -98,8 +102,13 @@ def tune_map(vmap, scans_dev, poses, vehicles, flush=None, refresh: bool = False
 
     key = workload_key("map", vmap.shape, vmap.cfg.res, int(statistics.median(int(p.shape[0]) for p in scans_dev)))
     best, entry = tuned(key, run, repeats=repeats, refresh=refresh)
-    vmap.set_tuning(*best)
+    apply_walk(vmap, best)
     return best, entry
+
+
+def apply_walk(vmap, c):
+    """Sets a walk candidate (seg_len, march_block, blocks_per_sm[, fused_ingest])."""
+    vmap.set_tuning(c[0], c[1], c[2], fused_ingest=c[3] if len(c) > 3 else 0)
 
 
 def extract_candidates(vmap):
@@ -168,6 +177,6 @@ def tune_batch(batch, maps, step_inputs, flush=None, refresh: bool = False, repe
 
     pts = sum(int(p.shape[0]) for p in step_inputs[0][1])
     key = workload_key(f"batch{len(maps)}", maps[0].shape, maps[0].cfg.res, pts)
-    best, entry = tuned(key, run, repeats=repeats, refresh=refresh)
+    best, entry = tuned(key, run, candidates=WALK_CANDIDATES, repeats=repeats, refresh=refresh)
     batch.set_tuning(*best)
     return best, entry

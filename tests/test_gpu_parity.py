@@ -85,22 +85,36 @@ def compare_stats(gm, om):
     assert st["points_in"] == om.stats.points_in
 
 
-def run_sequence(gv, params, scans, stride=3, check_each=True, products_each=False):
-    om = oracle.OracleMap(params)
+def new_map(gv, params, fused=False):
+    """A device map for the oracle's parameters; fused: one kernel lists and
+    walks each scan's segments (tuning fused_ingest)."""
     gm = gv.VoxelMap(gpu_config(gv, params))
+    if fused:
+        gm.set_fused_ingest(True)
+    return gm
+
+
+def run_sequence(gv, params, scans, stride=3, check_each=True, products_each=False, fused_too=False):
+    """Feeds the scans to the oracle and to a device map (and, with fused_too,
+    to a second device map on the fused ingest, checked the same way)."""
+    om = oracle.OracleMap(params)
+    gms = [new_map(gv, params)] + ([new_map(gv, params, fused=True)] if fused_too else [])
     for s in scans:
-        assert tuple(gm.origin_for_pose(s.vehicle_xyz)) == tuple(int(v) for v in oracle.origin_for_pose(params, s.vehicle_xyz))
+        assert tuple(gms[0].origin_for_pose(s.vehicle_xyz)) == tuple(int(v) for v in oracle.origin_for_pose(params, s.vehicle_xyz))
         om.shift_for_pose(s.vehicle_xyz)
         om.ingest(s.points, s.T_ws)
         pts = s.points
         if stride == 4:
             pts = np.concatenate([pts, np.ones((len(pts), 1), np.float32)], axis=1)
-        gm.update(s.vehicle_xyz, to_dev(pts), s.T_ws)
-        if check_each:
-            compare_voxels(gm, om)
-        if products_each:
-            compare_products(gm, om)
-    return gm, om
+        for gm in gms:
+            gm.update(s.vehicle_xyz, to_dev(pts), s.T_ws)
+            if check_each:
+                compare_voxels(gm, om)
+            if products_each:
+                compare_products(gm, om)
+    for gm in gms[1:]:
+        compare_stats(gm, om)
+    return gms[0], om
 
 
 def gen_workers():
@@ -111,7 +125,7 @@ def gen_workers():
 def test_single_scan(gv):
     s = synth.single_scan()
     params = params_for(synth.WORKLOADS["single_scan"]["map"])
-    gm, om = run_sequence(gv, params, [s])
+    gm, om = run_sequence(gv, params, [s], fused_too=True)
     compare_stats(gm, om)
     out, ref = compare_products(gm, om)
     assert np.count_nonzero(out["flags"] & 2) > 0 and np.count_nonzero(out["flags"] & 8) > 0
@@ -120,7 +134,7 @@ def test_single_scan(gv):
 def test_single_scan_stride4(gv):
     s = synth.single_scan()
     params = params_for(synth.WORKLOADS["single_scan"]["map"])
-    gm, om = run_sequence(gv, params, [s], stride=4)
+    gm, om = run_sequence(gv, params, [s], stride=4, fused_too=True)
     compare_products(gm, om)
 
 
@@ -131,7 +145,7 @@ def test_sequence_all_scans(gv):
     cfg, scans = synth.sequence_scans("sequence", workers=gen_workers())
     assert len(scans) == 20
     params = params_for(cfg.map)
-    gm, om = run_sequence(gv, params, scans, products_each=True)
+    gm, om = run_sequence(gv, params, scans, products_each=True, fused_too=True)
     compare_stats(gm, om)
 
 
@@ -140,12 +154,13 @@ def test_high_speed_scans_full_size(gv):
     # scans (12 voxels apart), state and every product after each
     cfg, scans = synth.sequence_scans("high_speed", n_scans=10, stride=1, workers=gen_workers())
     params = params_for(cfg.map)
-    gm, om = run_sequence(gv, params, scans, products_each=True)
+    gm, om = run_sequence(gv, params, scans, products_each=True, fused_too=True)
     compare_stats(gm, om)
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("n", [0, 1, 31, 33, 255, 257, 1000, 4099])
-def test_ragged_point_counts(gv, n):
+def test_ragged_point_counts(gv, n, fused):
     rng = np.random.default_rng(1000 + n)
     params = oracle.OracleParams(nx=40, ny=36, nz=20, res=0.2)
     pts = rng.normal(scale=3.0, size=(n, 3)).astype(np.float32)
@@ -157,7 +172,7 @@ def test_ragged_point_counts(gv, n):
     T = np.array([[math.cos(th), -math.sin(th), 0.01, 0.3], [math.sin(th), math.cos(th), -0.02, -0.1],
                   [-0.01, 0.02, 1.0, 1.5]])
     om = oracle.OracleMap(params)
-    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm = new_map(gv, params, fused)
     o = oracle.origin_for_pose(params, (0.1, -0.2, 0.0))
     om.shift_to(o)
     gm.shift(o)
@@ -168,25 +183,27 @@ def test_ragged_point_counts(gv, n):
     compare_products(gm, om)
 
 
-def test_sensor_outside_window_and_far_points(gv):
+@pytest.mark.parametrize("fused", [False, True])
+def test_sensor_outside_window_and_far_points(gv, fused):
     rng = np.random.default_rng(77)
     params = oracle.OracleParams(nx=24, ny=20, nz=10, res=0.25)
     pts = rng.uniform(-30, 30, size=(3000, 3)).astype(np.float32)
     T = np.array([[1.0, 0, 0, -9.0], [0, 1.0, 0, 2.0], [0, 0, 1.0, 0.4]])
     om = oracle.OracleMap(params, (0, 0, 0))
-    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm = new_map(gv, params, fused)
     om.ingest(pts, T)
     gm.ingest(to_dev(pts), T)
     compare_voxels(gm, om)
     compare_stats(gm, om)
 
 
-def test_shift_sequences_match(gv):
+@pytest.mark.parametrize("fused", [False, True])
+def test_shift_sequences_match(gv, fused):
     # random shifts (including ones past the window) of an accumulated map
     rng = np.random.default_rng(5)
     params = oracle.OracleParams(nx=30, ny=26, nz=14, res=0.2)
     om = oracle.OracleMap(params)
-    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm = new_map(gv, params, fused)
     o = np.array([-15, -13, -7])
     om.shift_to(o)
     gm.shift(o)
@@ -369,8 +386,9 @@ def test_cone_values_on_hand_built_grids(gv, case):
         np.testing.assert_array_equal(flags.cpu().numpy(), ref["flags"])
 
 
+@pytest.mark.parametrize("fused", [False, True])
 @pytest.mark.parametrize("case", range(6))
-def test_exact_ties_on_voxel_corners_edges_and_faces(gv, case):
+def test_exact_ties_on_voxel_corners_edges_and_faces(gv, case, fused):
     # res 0.25 m and coordinates on a 1/1024 m lattice make every quantised
     # endpoint exact; the sensor on a voxel corner and endpoints on the
     # quarter-voxel lattice make many crossings coincide (rays through voxel
@@ -394,7 +412,7 @@ def test_exact_ties_on_voxel_corners_edges_and_faces(gv, case):
                sv - np.array(dims) + 1, sv + np.array([-5, 2, -dims[2]]), sv + np.array([dims[0], 0, 0])]
     o = origins[case]
     om = oracle.OracleMap(params, tuple(int(v) for v in o))
-    gm = gv.VoxelMap(gpu_config(gv, params))
+    gm = new_map(gv, params, fused)
     gm.shift(tuple(int(v) for v in o))
     om.ingest(pts, T)
     gm.ingest(to_dev(pts), T)
