@@ -640,6 +640,61 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
     visits = 0;
 }
 
+// One step of the walk for every lane of the warp (all lanes call it): a
+// live lane visits its current voxel (in the window by construction) and
+// takes the next crossing group; the segment's crossing budget ends its walk
+// (live turns false). The step is branch-free: a lane that is not live keeps
+// stepping its (no longer read) state. item_n counts this lane's visits.
+template <bool kBatch, bool kSlot, bool kPow2>
+__device__ __forceinline__ void walk_step(Walk& w, bool& live, int lane, uint32_t* passes, uint32_t* spasses,
+                                          uint32_t vmap, unsigned long long* cnts, unsigned int& item_n) {
+    // On power-of-two windows the masked index cannot leave the map; on
+    // others the index is only formed for a voxel inside the window, so no
+    // access can leave the state arrays whatever the walk computes.
+    const bool visit = kPow2 ? live
+                             : live && (unsigned)w.cM < (unsigned)w.nM && (unsigned)w.cA < (unsigned)w.nA &&
+                                   (unsigned)w.cB < (unsigned)w.nB;
+    const uint32_t key = visit ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
+    // runs of neighbouring lanes in the same voxel merge their increments:
+    // the run's first lane adds the run's length
+    bool boundary;
+    if (kBatch) {
+        const unsigned long long kk =
+            visit ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
+        const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
+        boundary = lane == 0 || prev != kk;
+    } else {
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);  // every lane
+        boundary = lane == 0 || prev != key;
+    }
+    const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
+    if (visit && boundary && in_bounds(key, vmap, cnts)) {
+        const unsigned int after = starts & ~((2u << lane) - 1u);
+        const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
+        atomicAdd(passes + key, run);
+        if (kSlot && spasses) atomicAdd(spasses + key, run);
+    }
+    item_n += visit ? 1u : 0u;
+    const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
+    const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
+    const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
+    const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
+    if (kPow2) {
+        w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
+                ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
+                ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
+    } else {
+        w.cM = imad_s32(iM, w.dirM, w.cM);
+        w.cA = imad_s32(iA, w.dirA, w.cA);
+        w.cB = imad_s32(iB, w.dirB, w.cB);
+    }
+    w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
+    w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
+    w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
+    w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
+    live = live && w.rem > 0;
+}
+
 // Walks one segment per lane from its first in-window voxel until its
 // crossing budget runs out (live: the lane holds a segment), adding the pass
 // increments; returns the number of voxels this lane visited. All lanes of
@@ -647,59 +702,8 @@ __device__ __forceinline__ void flush_visits(const IngestArgs& a1, const IngestA
 template <bool kBatch, bool kSlot, bool kPow2>
 __device__ __forceinline__ unsigned int walk_run(Walk& w, bool live, int lane, uint32_t* passes, uint32_t* spasses,
                                                  uint32_t vmap, unsigned long long* cnts) {
-    // Visit the current voxel (in the window by construction), then take
-    // the next crossing group; the segment's crossing budget ends the walk.
-    // The step is branch-free: a lane that stops keeps stepping its
-    // (no longer read) state until the whole warp has stopped.
     unsigned int item_n = 0;
-    while (__any_sync(0xffffffffu, live)) {
-        // The voxel is in the window by construction. On power-of-two
-        // windows the masked index cannot leave the map anyway; on others
-        // the index is only formed for a voxel inside the window, so no
-        // access can leave the state arrays whatever the walk computes.
-        const bool visit = kPow2 ? live
-                                 : live && (unsigned)w.cM < (unsigned)w.nM && (unsigned)w.cA < (unsigned)w.nA &&
-                                       (unsigned)w.cB < (unsigned)w.nB;
-        const uint32_t key = visit ? (kPow2 ? w.key : walk_index(w)) : 0xffffffffu;
-        // runs of neighbouring lanes in the same voxel merge their
-        // increments: the run's first lane adds the run's length
-        bool boundary;
-        if (kBatch) {
-            const unsigned long long kk =
-                visit ? (unsigned long long)((kSlot && spasses) ? spasses + key : passes + key) : 0ull;
-            const unsigned long long prev = __shfl_up_sync(0xffffffffu, kk, 1);  // every lane
-            boundary = lane == 0 || prev != kk;
-        } else {
-            const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);  // every lane
-            boundary = lane == 0 || prev != key;
-        }
-        const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
-        if (visit && boundary && in_bounds(key, vmap, cnts)) {
-            const unsigned int after = starts & ~((2u << lane) - 1u);
-            const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
-            atomicAdd(passes + key, run);
-            if (kSlot && spasses) atomicAdd(spasses + key, run);
-        }
-        item_n += visit ? 1u : 0u;
-        const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
-        const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
-        const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
-        const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
-        if (kPow2) {
-            w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
-                    ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
-                    ((imad_u32((uint32_t)iB, w.stB, w.key)) & w.fmB);
-        } else {
-            w.cM = imad_s32(iM, w.dirM, w.cM);
-            w.cA = imad_s32(iA, w.dirA, w.cA);
-            w.cB = imad_s32(iB, w.dirB, w.cB);
-        }
-        w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
-        w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
-        w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
-        w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
-        live = live && w.rem > 0;
-    }
+    while (__any_sync(0xffffffffu, live)) walk_step<kBatch, kSlot, kPow2>(w, live, lane, passes, spasses, vmap, cnts, item_n);
     return item_n;
 }
 
