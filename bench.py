@@ -779,6 +779,8 @@ def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=
     r["walk_ms"] = [e[1].elapsed_time(e[2]) for e in wk_ev]
     r["rays_pass_ms"] = [e[0].elapsed_time(e[1]) for e in wk_ev]
     r["walk_visits"] = sw1["pass_visits"] - sw0["pass_visits"]
+    r["walk_hits"] = sw1["hits_in_window"] - sw0["hits_in_window"]
+    r["fused"] = len(tuning) > 3 and bool(tuning[3])
 
     # end to end through the public API with host buffers
     h2d = sum(p.numel() * 4 for p in host_pts) / ns
@@ -839,12 +841,15 @@ def walk_roofline(r, steps, red_coalesced, red_scattered, workload):
     reduction atomics on one 128-byte line, measured in this run); beside it
     the rate for scattered single-word atomics, which the walk's run merging
     can exceed."""
-    inc = r["walk_visits"] / steps
+    fused = r.get("fused", False)
+    # the fused kernel also lists the scan: its hit and lowest-return atomics count too
+    inc = (r["walk_visits"] + (2 * r["walk_hits"] if fused else 0)) / steps
     t = statistics.mean(r["walk_ms"]) * 1e-3
     achieved = inc / t
-    return {"kernel": "k_march", "bound": "l2_atomic", "achieved": achieved / 1e9, "peak": red_coalesced / 1e9,
+    kernel = "k_ingest_fused" if fused else "k_march"
+    return {"kernel": kernel, "bound": "l2_atomic", "achieved": achieved / 1e9, "peak": red_coalesced / 1e9,
             "unit": "Gincrement/s", "frac": achieved / red_coalesced,
-            "traffic": profile_traffic("k_march", "plain_" + workload),
+            "traffic": profile_traffic(kernel, "plain_" + workload),
             "launch_us": 1e6 * t, "increments_per_launch": inc,
             "peak_source": "measured in this run: 32-bit reduction atomics, 32 lanes on one 128-byte line per warp "
                            "instruction, over 64 MiB (gvom_microbench_red_coalesced)",
@@ -910,8 +915,8 @@ def plain_summary(args, r, workload, red_peak, red_coalesced, hbm_peak, peak_kin
             "roofline_extract": extract_roofline(r, ms, hbm_peak, peak_kind),
             "e2e": e2e_object(r), "gpu_launches_per_step": r["launches"] / steps,
             "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1],
-                       "march_blocks_per_sm": r["tuning"][2], "px_tile": r["ext_tuning"][0],
-                       "col_shape": r["ext_tuning"][1]},
+                       "march_blocks_per_sm": r["tuning"][2], "fused_ingest": int(r["fused"]),
+                       "px_tile": r["ext_tuning"][0], "col_shape": r["ext_tuning"][1]},
             "l2": L2_NOTE}
 
 
@@ -1088,8 +1093,8 @@ def main():
     if not args.no_next_rows:
         seq_cfg, seq_scans = seq_inputs
         seq_tuning = r["tuning"] if main_wl == "sequence" else (
-            tuple(other["tuning"][k] for k in ("seg_len", "march_block", "march_blocks_per_sm")) if other
-            else (16, 256, 0))
+            tuple(other["tuning"][k] for k in ("seg_len", "march_block", "march_blocks_per_sm", "fused_ingest"))
+            if other else (16, 256, 0, 0))
         seq_e2e = (r["rays_e2e"] / r["e2e_s"]) if main_wl == "sequence" else (
             other["e2e"]["serial"]["value"] if other else None)
         next_rows = run_next_rows(args, gv, torch, seq_cfg, seq_scans, seq_tuning, flush, stream, seq_e2e, hbm_peak)
@@ -1124,7 +1129,7 @@ def main():
         "gpu_launches": int(r["launches"]),
         "clocks": clocks.summary(),
         "tuning": {"seg_len": r["tuning"][0], "march_block": r["tuning"][1], "march_blocks_per_sm": r["tuning"][2],
-                   "px_tile": r["ext_tuning"][0], "col_shape": r["ext_tuning"][1],
+                   "fused_ingest": int(r["fused"]), "px_tile": r["ext_tuning"][0], "col_shape": r["ext_tuning"][1],
                    "search_us": r["tune_entry"].get("us"), "extract_search_us": r["ext_entry"].get("us")},
         other_wl: other,
         "batched": batched,
