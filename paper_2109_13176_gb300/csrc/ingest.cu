@@ -233,12 +233,7 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
     int q[3] = {0, 0, 0};
     float wz = 0.0f;
     const bool valid = i < a.n && point_ray(a, i, sensor_ok, q, wz);
-    int hit_in_window = 0;
-    int nseg = 0;
-    if (valid) {
-        hit_in_window = apply_hit(a, q, wz);
-        nseg = segments_of(a, qo, q);
-    }
+    const int nseg = valid ? segments_of(a, qo, q) : 0;
     if (i < a.n && in_bounds(ray_base + i, a.w.cap_points, a.s.counters))
         a.w.rays[ray_base + i] = make_int4(q[0], q[1], q[2], (int)((map_id << 16) | (unsigned)nseg));
 
@@ -288,6 +283,12 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
         off += __popc(m);
     }
 
+    // Up to here only the points and this scan's scratch were touched, so
+    // the work above overlaps the kernel before (the window shift). The map
+    // is touched only once that kernel is complete.
+    pdl_wait();
+    const int hit_in_window = valid ? apply_hit(a, q, wz) : 0;
+
     // Counters: one atomic per block and counter.
     __shared__ unsigned long long red[2][kRaysBlock / 32];
     unsigned long long v0 = valid ? 1ull : 0ull, v1 = (unsigned long long)hit_in_window;
@@ -309,8 +310,12 @@ __device__ __forceinline__ void rays_body(const IngestArgs& a, long long first, 
     __syncthreads();  // the shared arrays are reused by the caller's next block
 }
 
+// Launched with programmatic dependent launch, it starts before the kernel
+// ahead of it (the window shift) is complete: it reads the points and writes
+// the scratch, which no kernel before it still uses (the walk and the fused
+// ingest release their dependents only at their very end), and waits before
+// touching the map (in rays_body).
 __global__ void __launch_bounds__(kRaysBlock) k_rays(const IngestArgs a) {
-    pdl_wait();
     int qo[3];
     const bool sensor_ok = block_sensor(a, qo);
     rays_body(a, (long long)blockIdx.x * kRaysBlock, qo, sensor_ok, 0, 0u);
@@ -409,8 +414,13 @@ struct Walk {
     int nM, nA, nB;     // window extents
     int sM, sA, sB;     // 256 den per axis
     int nsM, nsA;       // -sM, -sA
-    int dMA, dMB, dAB;  // pairwise crossing-time differences
-    int tMA, tAM, tMB, tBM, tAB, tBA;  // tie thresholds: i first iff D_ij < t_ij
+    // Pairwise crossing-time differences D_ij, biased: x_ij = D_ij + t_ji - 1
+    // is >= 0 iff j's crossing comes first, and x_ij + c_ij = D_ij - t_ij is
+    // < 0 iff i's comes first (t_ij = 1 iff i moves up and j down, the
+    // tie-break; c_ij = 1 - t_ij - t_ji is 0 or 1). The step reads the
+    // decisions off sign bits.
+    int xMA, xMB, xAB;
+    int cMA, cMB, cAB;
     int rem;            // crossings left to take
     int rM, rA, rB;     // ring offsets
     uint32_t kM, kA, kB;  // strides of the state array per role
@@ -567,17 +577,21 @@ __device__ __forceinline__ bool walk_init(const IngestArgs& a, const int qo[3], 
     w.sB = 256 * den[2];
     w.nsM = -w.sM;
     w.nsA = -w.sA;
-    w.dMA = (int)((long long)num[0] * den[1] - (long long)num[1] * den[0]);
-    w.dMB = (int)((long long)num[0] * den[2] - (long long)num[2] * den[0]);
-    w.dAB = (int)((long long)num[1] * den[2] - (long long)num[2] * den[1]);
+    const int dMA = (int)((long long)num[0] * den[1] - (long long)num[1] * den[0]);
+    const int dMB = (int)((long long)num[0] * den[2] - (long long)num[2] * den[0]);
+    const int dAB = (int)((long long)num[1] * den[2] - (long long)num[2] * den[1]);
     // i first on equal t iff i moves up and j down: D_ij < t_ij with
     // t_ij = 1 then, else 0; j first iff D_ij > -t_ji.
-    w.tMA = rk[0] < rk[1];
-    w.tAM = rk[1] < rk[0];
-    w.tMB = rk[0] < rk[2];
-    w.tBM = rk[2] < rk[0];
-    w.tAB = rk[1] < rk[2];
-    w.tBA = rk[2] < rk[1];
+    const int tMA = rk[0] < rk[1], tAM = rk[1] < rk[0];
+    const int tMB = rk[0] < rk[2], tBM = rk[2] < rk[0];
+    const int tAB = rk[1] < rk[2], tBA = rk[2] < rk[1];
+    // |D_ij| <= 256 max(den) < 2^31, so the biased forms stay within int32
+    w.xMA = dMA + tAM - 1;
+    w.xMB = dMB + tBM - 1;
+    w.xAB = dAB + tBA - 1;
+    w.cMA = 1 - tMA - tAM;
+    w.cMB = 1 - tMB - tBM;
+    w.cAB = 1 - tAB - tBA;
     w.rem = rem;
     w.nM = n3[0];
     w.nA = n3[1];
@@ -675,10 +689,14 @@ __device__ __forceinline__ void walk_step(Walk& w, bool& live, int lane, uint32_
         if (kSlot && spasses) atomicAdd(spasses + key, run);
     }
     item_n += visit ? 1u : 0u;
-    const bool gM = !(w.dMA > -w.tAM) && !(w.dMB > -w.tBM);
-    const bool gA = !(w.dMA < w.tMA) && !(w.dAB > -w.tBA);
-    const bool gB = !(w.dMB < w.tMB) && !(w.dAB < w.tAB);
-    const int iM = gM ? 1 : 0, iA = gA ? 1 : 0, iB = gB ? 1 : 0;
+    // An axis steps iff no other axis's crossing comes first. y_ij = D_ij -
+    // t_ij as x_ij + c_ij^2 (c_ij is 0 or 1): a multiply-add, on the FMA pipe.
+    const int yMA = imad_s32(w.cMA, w.cMA, w.xMA);
+    const int yMB = imad_s32(w.cMB, w.cMB, w.xMB);
+    const int yAB = imad_s32(w.cAB, w.cAB, w.xAB);
+    const int iM = (int)((uint32_t)(w.xMA & w.xMB) >> 31);  // neither A nor B first
+    const int iA = (int)((uint32_t)(~yMA & w.xAB) >> 31);   // neither M nor B first
+    const int iB = (int)((uint32_t)(~(yMB | yAB)) >> 31);   // neither M nor A first
     if (kPow2) {
         w.key = ((imad_u32((uint32_t)iM, w.stM, w.key)) & w.fmM) |
                 ((imad_u32((uint32_t)iA, w.stA, w.key)) & w.fmA) |
@@ -688,9 +706,9 @@ __device__ __forceinline__ void walk_step(Walk& w, bool& live, int lane, uint32_
         w.cA = imad_s32(iA, w.dirA, w.cA);
         w.cB = imad_s32(iB, w.dirB, w.cB);
     }
-    w.dMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.dMA));
-    w.dMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.dMB));
-    w.dAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.dAB));
+    w.xMA = imad_s32(iM, w.sA, imad_s32(iA, w.nsM, w.xMA));
+    w.xMB = imad_s32(iM, w.sB, imad_s32(iB, w.nsM, w.xMB));
+    w.xAB = imad_s32(iA, w.sB, imad_s32(iB, w.nsA, w.xAB));
     w.rem = imad_s32(iM, -1, imad_s32(iA, -1, imad_s32(iB, -1, w.rem)));
     live = live && w.rem > 0;
 }
@@ -775,7 +793,6 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
         visits += item_visits;
     }
 
-    pdl_done();
     flush_visits(a1, descs, own, visits);
     if (!kBatch) {
         // the last block to finish empties the work list for the next scan
@@ -786,6 +803,10 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_march(const Inge
             a1.w.item_count[kListBlocksDone] = 0;
         }
     }
+    // dependents are released only now: the next scan's per-point pass writes
+    // the scratch before it waits
+    __syncthreads();
+    pdl_done();
 }
 
 // Fused ingest (tuning fused_ingest = 1): one persistent kernel whose warps
@@ -944,7 +965,6 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_ingest_fused(con
     // unwalked (no warp waits on a walking warp)
     if (gave_up && lane == 0) atomicOr(a.s.counters + kStatus, kStatusTimeout);
 
-    pdl_done();
     flush_visits(a, nullptr, 0u, visits);
     const unsigned int tv = __reduce_add_sync(0xffffffffu, n_valid);
     const unsigned int th = __reduce_add_sync(0xffffffffu, n_hit);
@@ -964,6 +984,9 @@ __global__ void __launch_bounds__(256, GVOM_MARCH_MIN_BLOCKS) k_ingest_fused(con
             ctr[kFBlocksDone] = 0;
         }
     }
+    // dependents are released only now (see k_march)
+    __syncthreads();
+    pdl_done();
 }
 
 // Empties the ring slots of `mask` at voxel i: their counts leave the
@@ -1107,6 +1130,9 @@ __device__ __forceinline__ void clear_voxel(const MapState& s, uint32_t k) {
 __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, int dz, long long n_xslab, long long n_cols,
                                 long long n_units) {
     pdl_wait();
+    // Every kernel after it waits for it before touching the map, so its
+    // dependents may launch at once: the per-point pass overlaps the shift.
+    pdl_done();
     const long long u = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (u >= n_units) return;
@@ -1141,7 +1167,6 @@ __global__ void k_shift_columns(MapState s, Geom g, int dx, int dy, int dz, long
             }
         }
     }
-    pdl_done();
 }
 
 // ---- batched maps ----------------------------------------------------------
