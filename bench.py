@@ -406,7 +406,7 @@ def profile_traffic(kernel: str, workload: str):
     src = os.path.join(ROOT, "paper_2109_13176_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")):
             with open(os.path.join(src, f), "rb") as fh:
                 h.update(fh.read())
     digest = h.hexdigest()[:16]
