@@ -542,6 +542,12 @@ __device__ __forceinline__ float key_height(uint32_t k) {
     return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
+// Order key of a height for the cone states (kNoKey: no ground). Finite
+// heights never map to kNoKey, which only a NaN's bits would give.
+constexpr uint32_t kNoKey = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t ground_key(float h) { return isnan(h) ? kNoKey : height_key(h); }
+
 // One warp sweeps the cone recurrence of one direction over the tile. The
 // cone grows along +u (sgn = +1) or -u (sgn = -1), u = the tile's row axis
 // (x) when along_x, else its column axis (y). With Q(c) = min(own key of c
@@ -551,42 +557,46 @@ __device__ __forceinline__ float key_height(uint32_t k) {
 // three cells. A cone whose ring-1 line lies outside the grid along u, or
 // whose distance passes neg_max_px, has no ground. Writes the cone value
 // (lowest height on the first ring with ground, NaN if none) of each
-// tile-interior pixel to val.
-__device__ void cone_sweep_warp(const ExtractParams& p, const float* Hs, int W, int R, int tile, int gx0, int gy0,
+// tile-interior pixel to val. Ks holds the heights' keys (ground_key), and
+// Qbuf two lines of W + 2 states whose first and last entries stay
+// kNoGround: the neighbours past the halo's edge, so no read tests v.
+__device__ void cone_sweep_warp(const ExtractParams& p, const uint32_t* Ks, int W, int R, int tile, int gx0, int gy0,
                                 bool along_x, int sgn, unsigned long long* Qbuf, float* val) {
-    // Hs rows are W + 1 floats apart and val rows tile + 1, so that the
+    // Ks rows are W + 1 words apart and val rows tile + 1, so that the
     // sweeps along y, whose lanes walk down a column, hit distinct banks
-    const int WP = W + 1, TP = tile + 1;
+    const int WP = W + 1, TP = tile + 1, QL = W + 2;
     const int lane = threadIdx.x & 31;
     const int nmaj = along_x ? p.g.nx : p.g.ny;
     const int g0 = along_x ? gx0 : gy0;  // global coordinate of tile row 0 along u
     const int first = sgn > 0 ? W - 1 : 0;
     const int last = sgn > 0 ? R : R + tile - 1;
     const int nsteps = sgn > 0 ? first - last + 1 : last - first + 1;
-    const unsigned long long dmax = (unsigned long long)p.neg_max_px << 32;
+    const uint32_t dmax = (uint32_t)p.neg_max_px;
     const float qnan = __int_as_float(0x7fffffff);
+    if (lane < 4) Qbuf[(lane >> 1) * QL + (lane & 1) * (W + 1)] = kNoGround;
+    __syncwarp();
     for (int st = 0; st < nsteps; ++st) {
         const int u = first - sgn * st;
-        unsigned long long* Qcur = Qbuf + (st & 1) * W;
-        const unsigned long long* Qprev = Qbuf + ((st + 1) & 1) * W;
+        unsigned long long* Qcur = Qbuf + (st & 1) * QL + 1;
+        const unsigned long long* Qprev = Qbuf + ((st + 1) & 1) * QL + 1;
         const int un = u + sgn;   // the ring-1 line (the previous step's)
         const int gun = g0 + un;  // its global coordinate
         const bool ring_ok = gun >= 0 && gun < nmaj && un >= 0 && un < W;
+        const int iu = u - R;
+        const bool out_row = iu >= 0 && iu < tile;  // this line holds tile pixels
         for (int v = lane; v < W; v += 32) {
             unsigned long long c = kNoGround;
             if (ring_ok) {
-                unsigned long long q = Qprev[v];
-                if (v > 0) q = min(q, Qprev[v - 1]);
-                if (v + 1 < W) q = min(q, Qprev[v + 1]);
-                if (q != kNoGround && (q >> 32) < dmax >> 32) c = q + (1ull << 32);
+                const unsigned long long q = min(min(Qprev[v - 1], Qprev[v]), Qprev[v + 1]);
+                // (kNoGround's distance word is above any limit)
+                if ((uint32_t)(q >> 32) < dmax) c = q + (1ull << 32);
             }
-            const float h = along_x ? Hs[u * WP + v] : Hs[v * WP + u];
-            const unsigned long long own = isnan(h) ? kNoGround : (unsigned long long)height_key(h);
-            Qcur[v] = min(own, c);
-            const int iu = u - R, iv = v - R;
-            if (iu >= 0 && iu < tile && iv >= 0 && iv < tile)
-                val[along_x ? iu * TP + iv : iv * TP + iu] =
-                    c != kNoGround ? key_height((uint32_t)c) : qnan;
+            const uint32_t k = along_x ? Ks[u * WP + v] : Ks[v * WP + u];
+            // own ground (distance 0) is nearer than any cone state
+            Qcur[v] = k != kNoKey ? (unsigned long long)k : c;
+            const int iv = v - R;
+            if (out_row && iv >= 0 && iv < tile)
+                val[along_x ? iu * TP + iv : iv * TP + iu] = c != kNoGround ? key_height((uint32_t)c) : qnan;
         }
         __syncwarp();
     }
@@ -659,19 +669,29 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     const int R = max(p.neg_max_px, r);
     const int W = tile + 2 * R;
     const int WP = W + 1, TP = tile + 1;                // padded row strides (no bank conflicts down columns)
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const int tt = tile * tile;
     const int tv = tile * TP;                           // one direction's padded cone values
-    unsigned long long* Qbufs = reinterpret_cast<unsigned long long*>(smem);  // 4 * 2W cone keys
-    float* Hs = smem + 16 * W;                          // W rows of WP heights, NaN outside the grid
-    float* vals = Hs + W * WP;                          // 4 * tile rows of TP cone values
+    const int QL = W + 2;                               // one cone line with its two edge entries
+    unsigned long long* Qbufs = reinterpret_cast<unsigned long long*>(smem);  // 4 * 2 lines of cone states
+    float* Hs = smem + 16 * QL;                         // W rows of WP heights, NaN outside the grid
+    uint32_t* Ks = reinterpret_cast<uint32_t*>(Hs + W * WP);  // their keys (ground_key)
+    float* vals = reinterpret_cast<float*>(Ks + W * WP);      // 4 * tile rows of TP cone values
     const int gx0 = tx0 - R, gy0 = ty0 - R;             // global coordinates of tile cell (0, 0)
     const float qnan = __int_as_float(0x7fffffff);
+    // t / tile for t < 2^16 as a high multiply: M = ceil(2^32 / tile) is exact
+    // there (the error t (M - 2^32 / tile) / 2^32 < 2^-16 stays below 1 / tile)
+    const uint32_t M = 0xffffffffu / (uint32_t)tile + 1u;
 
-    for (int t = threadIdx.x; t < W * W; t += blockDim.x) {
-        const int i = t / W, j = t % W;
-        const int gx = gx0 + i, gy = gy0 + j;
-        Hs[i * WP + j] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
+    for (int i = warp; i < W; i += nwarps) {
+        const int gx = gx0 + i;
+        const bool row_in = gx >= 0 && gx < nx;
+        for (int j = lane; j < W; j += 32) {
+            const int gy = gy0 + j;
+            const float h = (row_in && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
+            Hs[i * WP + j] = h;
+            Ks[i * WP + j] = ground_key(h);
+        }
     }
     __syncthreads();
 
@@ -681,7 +701,7 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     const int fit0 = split ? 128 : 0;
     if ((slope || rough) && (!split || warp >= 4)) {
         for (int t = (int)threadIdx.x - fit0; t < tt; t += (int)blockDim.x - fit0) {
-            const int li = t / tile, lj = t % tile;
+            const int li = (int)__umulhi((uint32_t)t, M), lj = t - li * tile;
             const int cx = tx0 + li, cy = ty0 + lj;
             if (cx >= nx || cy >= ny) continue;
             const int ci = li + R, cj = lj + R;
@@ -702,11 +722,11 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     }
     if (flags) {
         if (warp < 4)
-            cone_sweep_warp(p, Hs, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * W,
+            cone_sweep_warp(p, Ks, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
                             vals + warp * tv);
         __syncthreads();
         for (int t = threadIdx.x; t < tt; t += blockDim.x) {
-            const int li = t / tile, lj = t % tile;
+            const int li = (int)__umulhi((uint32_t)t, M), lj = t - li * tile;
             const int cx = tx0 + li, cy = ty0 + lj;
             if (cx >= nx || cy >= ny) continue;
             if (!isnan(Hs[(li + R) * WP + (lj + R)])) continue;
@@ -796,9 +816,11 @@ __global__ void __launch_bounds__(kPxBlockBatch, 8) k_slope_negative_batch(Batch
 }
 
 size_t slope_negative_smem_tile(int R, int tile) {
+    // cone lines (4 directions x 2 lines of W + 2 states), heights and their
+    // keys (W rows of W + 1), cone values (4 x tile rows of tile + 1)
     const int W = tile + 2 * R;
-    return sizeof(unsigned long long) * 8 * (size_t)W +
-           sizeof(float) * ((size_t)W * (W + 1) + 4 * (size_t)tile * (tile + 1));
+    return sizeof(unsigned long long) * 8 * (size_t)(W + 2) + 2 * sizeof(float) * (size_t)W * (W + 1) +
+           sizeof(float) * 4 * (size_t)tile * (tile + 1);
 }
 
 
