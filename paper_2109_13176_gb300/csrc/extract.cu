@@ -560,8 +560,9 @@ __device__ __forceinline__ uint32_t ground_key(float h) { return isnan(h) ? kNoK
 // tile-interior pixel to val. Ks holds the heights' keys (ground_key), and
 // Qbuf two lines of W + 2 states whose first and last entries stay
 // kNoGround: the neighbours past the halo's edge, so no read tests v.
+template <bool along_x>
 __device__ void cone_sweep_warp(const ExtractParams& p, const uint32_t* Ks, int W, int R, int tile, int gx0, int gy0,
-                                bool along_x, int sgn, unsigned long long* Qbuf, float* val) {
+                                int sgn, unsigned long long* Qbuf, float* val) {
     // Ks rows are W + 1 words apart and val rows tile + 1, so that the
     // sweeps along y, whose lanes walk down a column, hit distinct banks
     const int WP = W + 1, TP = tile + 1, QL = W + 2;
@@ -584,6 +585,7 @@ __device__ void cone_sweep_warp(const ExtractParams& p, const uint32_t* Ks, int 
         const bool ring_ok = gun >= 0 && gun < nmaj && un >= 0 && un < W;
         const int iu = u - R;
         const bool out_row = iu >= 0 && iu < tile;  // this line holds tile pixels
+#pragma unroll 2
         for (int v = lane; v < W; v += 32) {
             unsigned long long c = kNoGround;
             if (ring_ok) {
@@ -721,9 +723,12 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
         }
     }
     if (flags) {
-        if (warp < 4)
-            cone_sweep_warp(p, Ks, W, R, tile, gx0, gy0, warp < 2, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
-                            vals + warp * tv);
+        if (warp < 2)
+            cone_sweep_warp<true>(p, Ks, W, R, tile, gx0, gy0, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
+                                  vals + warp * tv);
+        else if (warp < 4)
+            cone_sweep_warp<false>(p, Ks, W, R, tile, gx0, gy0, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
+                                   vals + warp * tv);
         __syncthreads();
         for (int t = threadIdx.x; t < tt; t += blockDim.x) {
             const int li = (int)__umulhi((uint32_t)t, M), lj = t - li * tile;
