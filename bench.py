@@ -549,6 +549,7 @@ def run_next_rows(args, gv, torch, cfg, scans, tuning, flush, stream, serial_e2e
     """The widened rows on the plain-sequence workload: the asynchronous
     pipeline end to end, the lookup-table export, a 10-scan buffer, and four
     sensors per scan folded in one launch."""
+    from paper_2109_13176_gb300 import tune
     ms = cfg.map
     dev_pts = [torch.from_numpy(s.points).cuda() for s in scans]
     host_pts = [torch.from_numpy(s.points).pin_memory() for s in scans]

@@ -51,3 +51,43 @@ def test_traffic_record_ignores_a_stale_digest(tmp_path, monkeypatch):
 def test_host_cpu_description():
     h = bench.host_cpu()
     assert h["nproc"] == (os.cpu_count() or 0) and isinstance(h["model"], str) and h["model"]
+
+
+def test_bench_functions_name_only_defined_globals():
+    # every name a function of bench.py loads is a local, a module-level name
+    # or a builtin (a missing import would otherwise surface only in a leg
+    # that runs on a GPU)
+    import ast
+    import builtins
+    import os
+    src = open(os.path.join(os.path.dirname(__file__), "..", "bench.py")).read()
+    tree = ast.parse(src)
+    top = set()
+    for n in tree.body:
+        if isinstance(n, (ast.FunctionDef, ast.ClassDef)):
+            top.add(n.name)
+        elif isinstance(n, (ast.Import, ast.ImportFrom)):
+            top.update((a.asname or a.name).split(".")[0] for a in n.names)
+        elif isinstance(n, ast.Assign):
+            top.update(t.id for t in n.targets if isinstance(t, ast.Name))
+    missing = []
+    for f in (n for n in tree.body if isinstance(n, ast.FunctionDef)):
+        local = set()
+        for node in ast.walk(f):
+            if isinstance(node, ast.Name) and isinstance(node.ctx, (ast.Store, ast.Del)):
+                local.add(node.id)
+            elif isinstance(node, (ast.FunctionDef, ast.Lambda)):
+                if isinstance(node, ast.FunctionDef):
+                    local.add(node.name)
+                a = node.args
+                local.update(x.arg for x in a.args + a.kwonlyargs + a.posonlyargs)
+                local.update(x.arg for x in (a.vararg, a.kwarg) if x)
+            elif isinstance(node, (ast.Import, ast.ImportFrom)):
+                local.update((a.asname or a.name).split(".")[0] for a in node.names)
+            elif isinstance(node, ast.ExceptHandler) and node.name:
+                local.add(node.name)
+        for node in ast.walk(f):
+            if isinstance(node, ast.Name) and isinstance(node.ctx, ast.Load):
+                if node.id not in local and node.id not in top and not hasattr(builtins, node.id):
+                    missing.append((f.name, node.id, node.lineno))
+    assert not missing, missing
