@@ -684,7 +684,8 @@ __device__ __forceinline__ void walk_step(Walk& w, bool& live, int lane, uint32_
     const unsigned int starts = __ballot_sync(0xffffffffu, boundary);
     if (visit && boundary && in_bounds(key, vmap, cnts)) {
         const unsigned int after = starts & ~((2u << lane) - 1u);
-        const uint32_t run = (uint32_t)((after ? __ffs(after) - 1 : 32) - lane);
+        // the next run's first lane, or 32 past the warp's end (clz(0) = 32)
+        const uint32_t run = (uint32_t)(__clz(__brev(after)) - lane);
         atomicAdd(passes + key, run);
         if (kSlot && spasses) atomicAdd(spasses + key, run);
     }
@@ -721,7 +722,12 @@ template <bool kBatch, bool kSlot, bool kPow2>
 __device__ __forceinline__ unsigned int walk_run(Walk& w, bool live, int lane, uint32_t* passes, uint32_t* spasses,
                                                  uint32_t vmap, unsigned long long* cnts) {
     unsigned int item_n = 0;
-    while (__any_sync(0xffffffffu, live)) walk_step<kBatch, kSlot, kPow2>(w, live, lane, passes, spasses, vmap, cnts, item_n);
+    // two steps per vote: a lane that stops after the first one takes a
+    // second step that visits nothing
+    while (__any_sync(0xffffffffu, live)) {
+        walk_step<kBatch, kSlot, kPow2>(w, live, lane, passes, spasses, vmap, cnts, item_n);
+        walk_step<kBatch, kSlot, kPow2>(w, live, lane, passes, spasses, vmap, cnts, item_n);
+    }
     return item_n;
 }
 
