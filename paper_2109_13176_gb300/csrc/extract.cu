@@ -604,6 +604,72 @@ __device__ void cone_sweep_warp(const ExtractParams& p, const uint32_t* Ks, int 
     }
 }
 
+// The same sweep with the cone line held in registers when the halo is at
+// most 32 * kCells wide: lane l holds cells v = l and (kCells = 2) v = l + 32,
+// and reads its neighbours' states of the previous line by warp shuffles
+// instead of shared memory. Cells v >= W stay kNoGround (the line's edge).
+template <bool along_x, int kCells>
+__device__ __forceinline__ void cone_sweep_regs(const ExtractParams& p, const uint32_t* Ks, int W, int R, int tile,
+                                                int gx0, int gy0, int sgn, float* val) {
+    const int WP = W + 1, TP = tile + 1;
+    const int lane = threadIdx.x & 31;
+    const int nmaj = along_x ? p.g.nx : p.g.ny;
+    const int g0 = along_x ? gx0 : gy0;
+    const int first = sgn > 0 ? W - 1 : 0;
+    const int last = sgn > 0 ? R : R + tile - 1;
+    const int nsteps = sgn > 0 ? first - last + 1 : last - first + 1;
+    const uint32_t dmax = (uint32_t)p.neg_max_px;
+    const float qnan = __int_as_float(0x7fffffff);
+    unsigned long long q0 = kNoGround, q1 = kNoGround;  // the previous line's states of this lane's cells
+    for (int st = 0; st < nsteps; ++st) {
+        const int u = first - sgn * st;
+        const int un = u + sgn;
+        const int gun = g0 + un;
+        const bool ring_ok = gun >= 0 && gun < nmaj && un >= 0 && un < W;
+        const int iu = u - R;
+        const bool out_row = iu >= 0 && iu < tile;
+        // neighbours v - 1 and v + 1 of each cell on the previous line
+        unsigned long long l0, r0, l1 = kNoGround, r1 = kNoGround;
+        if (kCells == 1) {
+            l0 = __shfl_up_sync(0xffffffffu, q0, 1);
+            r0 = __shfl_down_sync(0xffffffffu, q0, 1);
+            if (lane == 0) l0 = kNoGround;
+            if (lane == 31) r0 = kNoGround;
+        } else {
+            // cell 31's right neighbour is lane 0's second cell, cell 32's left
+            // one lane 31's first cell
+            l0 = __shfl_up_sync(0xffffffffu, q0, 1);
+            r0 = __shfl_sync(0xffffffffu, lane == 0 ? q1 : q0, (lane + 1) & 31);
+            l1 = __shfl_sync(0xffffffffu, lane == 31 ? q0 : q1, (lane + 31) & 31);
+            r1 = __shfl_down_sync(0xffffffffu, q1, 1);
+            if (lane == 0) l0 = kNoGround;
+            if (lane == 31) r1 = kNoGround;
+        }
+#pragma unroll
+        for (int k = 0; k < kCells; ++k) {
+            const int v = lane + 32 * k;
+            const unsigned long long qm = k == 0 ? q0 : q1, ql = k == 0 ? l0 : l1, qr = k == 0 ? r0 : r1;
+            unsigned long long c = kNoGround;
+            if (ring_ok) {
+                const unsigned long long qq = min(min(ql, qm), qr);
+                if ((uint32_t)(qq >> 32) < dmax) c = qq + (1ull << 32);
+            }
+            unsigned long long nq = kNoGround;
+            if (v < W) {
+                const uint32_t kk = along_x ? Ks[u * WP + v] : Ks[v * WP + u];
+                nq = kk != kNoKey ? (unsigned long long)kk : c;
+                const int iv = v - R;
+                if (out_row && iv >= 0 && iv < tile)
+                    val[along_x ? iu * TP + iv : iv * TP + iu] = c != kNoGround ? key_height((uint32_t)c) : qnan;
+            }
+            if (k == 0)
+                q0 = nq;
+            else
+                q1 = nq;
+        }
+    }
+}
+
 // Least-squares plane z = a i + b j + c over the defined pixels of the
 // (2r+1)^2 window around tile cell (ci, cj), z relative to the centre
 // height h0. The normal matrix is integer (exact, so is the singularity
@@ -723,12 +789,27 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
         }
     }
     if (flags) {
-        if (warp < 2)
-            cone_sweep_warp<true>(p, Ks, W, R, tile, gx0, gy0, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
-                                  vals + warp * tv);
-        else if (warp < 4)
-            cone_sweep_warp<false>(p, Ks, W, R, tile, gx0, gy0, (warp & 1) ? -1 : 1, Qbufs + warp * 2 * QL,
-                                   vals + warp * tv);
+        // warp w < 4 sweeps cone w (+x, -x, +y, -y); lines of up to 64 cells
+        // live in registers, wider ones in shared memory
+        if (warp < 4) {
+            const int sgn = (warp & 1) ? -1 : 1;
+            float* const val = vals + warp * tv;
+            if (W <= 32) {
+                if (warp < 2)
+                    cone_sweep_regs<true, 1>(p, Ks, W, R, tile, gx0, gy0, sgn, val);
+                else
+                    cone_sweep_regs<false, 1>(p, Ks, W, R, tile, gx0, gy0, sgn, val);
+            } else if (W <= 64) {
+                if (warp < 2)
+                    cone_sweep_regs<true, 2>(p, Ks, W, R, tile, gx0, gy0, sgn, val);
+                else
+                    cone_sweep_regs<false, 2>(p, Ks, W, R, tile, gx0, gy0, sgn, val);
+            } else if (warp < 2) {
+                cone_sweep_warp<true>(p, Ks, W, R, tile, gx0, gy0, sgn, Qbufs + warp * 2 * QL, val);
+            } else {
+                cone_sweep_warp<false>(p, Ks, W, R, tile, gx0, gy0, sgn, Qbufs + warp * 2 * QL, val);
+            }
+        }
         __syncthreads();
         for (int t = threadIdx.x; t < tt; t += blockDim.x) {
             const int li = (int)__umulhi((uint32_t)t, M), lj = t - li * tile;

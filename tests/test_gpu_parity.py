@@ -150,9 +150,11 @@ def test_sequence_all_scans(gv):
 
 
 def test_high_speed_scans_full_size(gv):
-    # the 512 x 512 x 64 map at 0.1 m: the workload's first 10 consecutive
-    # scans (12 voxels apart), state and every product after each
-    cfg, scans = synth.sequence_scans("high_speed", n_scans=10, stride=1, workers=gen_workers())
+    # the 512 x 512 x 64 map at 0.1 m: all 40 consecutive scans the benchmark
+    # times (12 voxels apart), state and every product after each
+    cfg, scans = synth.sequence_scans("high_speed", n_scans=40, stride=1, seed=synth.SEEDS["high_speed"],
+                                      workers=gen_workers())
+    assert len(scans) == 40
     params = params_for(cfg.map)
     gm, om = run_sequence(gv, params, scans, products_each=True, fused_too=True)
     compare_stats(gm, om)
