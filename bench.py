@@ -397,19 +397,41 @@ def read_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def profile_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+# the CUDA source each profiled kernel is compiled from (besides the headers)
+KERNEL_SOURCES = {"k_march": "ingest.cu", "k_rays": "ingest.cu", "k_ingest": "ingest.cu",
+                  "k_ingest_fused": "ingest.cu", "k_columns_tma": "extract.cu", "k_slope_negative": "extract.cu"}
+
+
+def source_digest(kernel: str) -> str:
+    """Digest of the sources a kernel is built from: its .cu file (every .cu
+    file for a kernel not listed, or whose file is missing), the library's
+    headers and the public header. A change elsewhere leaves it unchanged."""
     import hashlib
+    src = os.path.join(ROOT, "paper_2109_13176_gb300", "csrc")
+    names = sorted(os.listdir(src))
+    own = KERNEL_SOURCES.get(kernel)
+    if own in names:
+        files = [own] + [f for f in names if f.endswith((".cuh", ".h"))]
+    else:
+        files = [f for f in names if f.endswith((".cu", ".cuh", ".h"))]
+    paths = [os.path.join(src, f) for f in files]
+    pub = os.path.join(ROOT, "include", "gvom.h")
+    if os.path.exists(pub):
+        paths.append(pub)
+    h = hashlib.sha256()
+    for q in paths:
+        with open(q, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    sources are the ones it was measured on."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    src = os.path.join(ROOT, "paper_2109_13176_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(src, f), "rb") as fh:
-                h.update(fh.read())
-    digest = h.hexdigest()[:16]
+    digest = source_digest(kernel)
     with open(p) as fh:
         for line in fh:
             parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)

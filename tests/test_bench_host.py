@@ -91,3 +91,23 @@ def test_bench_functions_name_only_defined_globals():
                 if node.id not in local and node.id not in top and not hasattr(builtins, node.id):
                     missing.append((f.name, node.id, node.lineno))
     assert not missing, missing
+
+
+def test_traffic_digest_follows_the_kernels_own_sources(tmp_path, monkeypatch):
+    # a kernel's DRAM bytes stay valid while its own .cu file and the headers
+    # are unchanged; another kernel's file does not matter
+    csrc = tmp_path / "paper_2109_13176_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "ingest.cu").write_text("// walk\n")
+    (csrc / "extract.cu").write_text("// columns\n")
+    (csrc / "gvom_internal.h").write_text("// shared\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.source_digest("k_march")
+    (csrc / "extract.cu").write_text("// columns, changed\n")
+    assert bench.source_digest("k_march") == d0
+    assert bench.source_digest("k_columns_tma") != d0
+    (csrc / "ingest.cu").write_text("// walk, changed\n")
+    assert bench.source_digest("k_march") != d0
+    d1 = bench.source_digest("k_march")
+    (csrc / "gvom_internal.h").write_text("// shared, changed\n")
+    assert bench.source_digest("k_march") != d1
