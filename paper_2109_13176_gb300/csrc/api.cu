@@ -138,9 +138,10 @@ int ensure_capacity(gvom_map* m, long long n, cudaStream_t st) {
     m->w.cap_items = 0;
     e = cudaMalloc(&m->w.rays, sizeof(int4) * (size_t)cap);
     // 16 bytes per entry (the fused ingest's int4 entries), all zero: no
-    // entry carries a fused scan's tag before that scan writes it
+    // entry carries a fused scan's tag before that scan writes it (cleared on
+    // the caller's stream, ahead of the kernels that will read the list)
     if (e == cudaSuccess) e = cudaMalloc(&m->w.items, sizeof(int4) * (size_t)(cap * per_ray));
-    if (e == cudaSuccess) e = cudaMemset(m->w.items, 0, sizeof(int4) * (size_t)(cap * per_ray));
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->w.items, 0, sizeof(int4) * (size_t)(cap * per_ray), st);
     if (e != cudaSuccess) {
         cudaFree(m->w.rays);
         cudaFree(m->w.items);
