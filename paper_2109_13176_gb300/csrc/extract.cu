@@ -751,16 +751,34 @@ __device__ __forceinline__ void tile_body(const ExtractParams& p, const float* _
     // there (the error t (M - 2^32 / tile) / 2^32 < 2^-16 stays below 1 / tile)
     const uint32_t M = 0xffffffffu / (uint32_t)tile + 1u;
 
-    for (int i = warp; i < W; i += nwarps) {
-        const int gx = gx0 + i;
-        const bool row_in = gx >= 0 && gx < nx;
-        for (int j = lane; j < W; j += 32) {
-            const int gy = gy0 + j;
-            const float h = (row_in && gy >= 0 && gy < ny) ? height[(size_t)gx * ny + gy] : qnan;
-            Hs[i * WP + j] = h;
-            Ks[i * WP + j] = ground_key(h);
+    // the tile and its halo: each warp takes rows warp, warp + nwarps, ...,
+    // four rows (two 32-cell halves each) per round with all eight loads
+    // issued before any shared store, so their latencies overlap
+    constexpr int kRows = 4;
+    for (int i0 = warp; i0 < W; i0 += nwarps * kRows)
+        for (int j0 = 0; j0 < W; j0 += 64) {
+            float hv[kRows][2];
+#pragma unroll
+            for (int b = 0; b < kRows; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = i0 + b * nwarps, j = j0 + lane + 32 * c;
+                    const int gx = gx0 + i, gy = gy0 + j;
+                    hv[b][c] = (i < W && j < W && gx >= 0 && gx < nx && gy >= 0 && gy < ny)
+                                   ? height[(size_t)gx * ny + gy]
+                                   : qnan;
+                }
+#pragma unroll
+            for (int b = 0; b < kRows; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = i0 + b * nwarps, j = j0 + lane + 32 * c;
+                    if (i < W && j < W) {
+                        Hs[i * WP + j] = hv[b][c];
+                        Ks[i * WP + j] = ground_key(hv[b][c]);
+                    }
+                }
         }
-    }
     __syncthreads();
 
     // with eight warps, warps 0-3 sweep the four cones while warps 4-7 fit
