@@ -173,3 +173,26 @@ def test_fused_flag_while_capturing_a_graph(gv):
         np.testing.assert_array_equal(x, y)
     ref.close()
     cap.close()
+
+
+def test_fused_ingest_on_a_side_stream(gv):
+    # the first ingest grows the map's scratch (its list is cleared on the
+    # caller's stream, before the fused kernel reads the tags): a map fed on a
+    # side stream equals a two-kernel map fed on the default stream
+    cfg, scans = synth.sequence_scans("sequence", n_scans=3, stride=2)
+    ms = cfg.map
+    ref = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res)
+    fu = gv.VoxelMap(nx=ms.nx, ny=ms.ny, nz=ms.nz, res=ms.res)
+    fu.set_fused_ingest(True)
+    side = torch.cuda.Stream()
+    for s in scans:
+        p = torch.from_numpy(s.points).cuda()
+        torch.cuda.synchronize()
+        ref.update(s.vehicle_xyz, p, s.T_ws)
+        with torch.cuda.stream(side):
+            fu.update(s.vehicle_xyz, p, s.T_ws, stream=side)
+        side.synchronize()
+    torch.cuda.synchronize()
+    same_state(voxels_and_stats(fu), voxels_and_stats(ref))
+    ref.close()
+    fu.close()
