@@ -57,3 +57,19 @@ def test_cached_entry_of_another_shape_is_searched_again(tmp_path, monkeypatch):
     run_b, calls_b = fake_run((8, 256, 0))
     best_b, _ = tune.tuned("k", run_b, candidates=tune.WALK_CANDIDATES, repeats=1, refresh=True)
     assert best_b == (8, 256, 0) and len(calls_b) == 2 * len(tune.WALK_CANDIDATES)
+
+
+def test_apply_walk_passes_the_fused_flag():
+    # a three-field candidate (a batch's walk shape) keeps the two-kernel
+    # ingest; a four-field one sets the fused-ingest flag it names
+    calls = []
+
+    class FakeMap:
+        def set_tuning(self, *args, **kw):
+            calls.append((args, kw))
+
+    tune.apply_walk(FakeMap(), (16, 256, 0))
+    tune.apply_walk(FakeMap(), (48, 128, 0, 1))
+    assert calls == [((16, 256, 0), {"fused_ingest": 0}), ((48, 128, 0), {"fused_ingest": 1})]
+    assert all(len(c) == 4 for c in tune.CANDIDATES) and all(len(c) == 3 for c in tune.WALK_CANDIDATES)
+    assert {c[3] for c in tune.CANDIDATES} == {0, 1}
