@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--batched-maps", type=int, default=64)
     ap.add_argument("--batched-steps", type=int, default=10, help="timed steps of the batched leg")
     ap.add_argument("--retune", action="store_true", help="ignore cached tuning and search again")
+    ap.add_argument("--tuning", default=None,
+                    help="walk shape seg_len/march_block/blocks_per_sm/fused_ingest for the plain legs instead of "
+                         "the tuner's (e.g. 64/128/0/1 for the fused ingest)")
     ap.add_argument("--no-served", action="store_true", help="skip the served leg")
     ap.add_argument("--served-seconds", type=float, default=60.0, help="length of the replayed arrival stream")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the pipeline / LUT / buffer / multi-sensor legs")
@@ -727,8 +730,14 @@ def measure_plain(args, gv, tune, torch, inputs, flush, stream, world=1, clocks=
     out = gmap.alloc_maps()
     # launch shape for this workload: cached, or searched on its first scans
     nt = min(4, ns)
-    tuning, tune_entry = tune.tune_map(gmap, dev_pts[:nt], [s.T_ws for s in scans[:nt]],
-                                       [s.vehicle_xyz for s in scans[:nt]], flush=flush, refresh=args.retune)
+    if getattr(args, "tuning", None):
+        # a walk shape named on the command line instead of the tuner's
+        tuning = tuple(int(v) for v in args.tuning.split("/"))
+        tune.apply_walk(gmap, tuning)
+        tune_entry = {"forced": args.tuning}
+    else:
+        tuning, tune_entry = tune.tune_map(gmap, dev_pts[:nt], [s.T_ws for s in scans[:nt]],
+                                           [s.vehicle_xyz for s in scans[:nt]], flush=flush, refresh=args.retune)
     # extraction shapes, on the state those scans left
     ext_tuning, ext_entry = tune.tune_extract(gmap, out, flush=flush, refresh=args.retune)
     gmap.reset((0, 0, 0))
