@@ -134,8 +134,10 @@ typedef struct gvom_maps_out {
  * extractions keep their built-in shapes.
  * Ingest of one map (gvom_ingest_scan): fused_ingest = 1 has one persistent
  * cooperative kernel (a grid of resident blocks) both list and walk a scan's
- * segments, its warps taking point tiles and 32-segment chunks of the list
- * from shared counters; 0 runs the two kernels (list, then walk). The fused
+ * segments: each warp lists its own 32-point tiles, then walks its own
+ * 32-entry chunks of the list as their entries appear; 0 runs the two
+ * kernels (list, then walk). The two kernels are faster on the workloads
+ * measured; the autotuner times both. The fused
  * kernel serves maps without a scan buffer, with at most 4096 segments per
  * ray, on streams that are not capturing a graph; other ingests use the two
  * kernels whatever this field says.
